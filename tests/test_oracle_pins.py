@@ -1,0 +1,277 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a closed form, an
+identity derived independently of the code, a brute-force derivative, a
+special case with a known solution, or a value printed in the paper.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import ipm, mesh, operators as ops
+from ot_inputs import make_density
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- geometry
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_mesh_counts_and_nesting(n):
+    """N' = 2n^2, N = 4N' = 8n^2, N'_e = 3n^2-2n, N_e = 12n^2-4n = 2N'_e + 4N' - ... (Sec. 2.1)."""
+    t = mesh.two_level_square(n)
+    assert t.coarse.ncell == 2 * n * n and t.fine.ncell == 8 * n * n
+    assert t.coarse.nedge == 3 * n * n - 2 * n
+    # fine interior edges: each coarse interior edge splits in two, plus 3 new edges per coarse cell
+    assert t.fine.nedge == 2 * t.coarse.nedge + 3 * t.coarse.ncell
+    assert np.isclose(t.coarse.area.sum(), 1.0) and np.isclose(t.fine.area.sum(), 1.0)
+    counts = np.bincount(t.parent, minlength=t.coarse.ncell)
+    assert np.all(counts == 4)
+    child_area = np.bincount(t.parent, weights=t.fine.area)
+    assert np.allclose(child_area, t.coarse.area, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_geometry_closed_form(n):
+    """Right triangles: circumcentre = hypotenuse midpoint, |e|/|w| = 1 on legs, 3 on hypotenuses
+    (barycentre distance sqrt(2) h/3, reading R1), lambda = 1/2 everywhere (reading R2)."""
+    for m, tm in ((n, mesh.build_mesh(*mesh.square_grid(n))), (2 * n, mesh.two_level_square(n).fine)):
+        h = 1.0 / m
+        p = tm.xy[tm.tri]
+        side = np.stack([np.hypot(*(p[:, (k + 1) % 3] - p[:, k]).T) for k in range(3)], 1)
+        hyp = np.argmax(side, 1)
+        mid = np.array([(p[c, hyp[c]] + p[c, (hyp[c] + 1) % 3]) / 2 for c in range(tm.ncell)])
+        assert np.allclose(tm.centre, mid, atol=1e-14)
+        legs = np.isclose(tm.edge_len, h)
+        diag = np.isclose(tm.edge_len, np.sqrt(2) * h)
+        assert np.all(legs | diag)
+        assert np.array_equal(diag, tm.degenerate)
+        assert np.allclose(tm.edge_dist[legs], h)
+        assert np.allclose(tm.edge_dist[diag], np.sqrt(2) * h / 3)
+        assert np.allclose(tm.edge_lambda, 0.5)
+
+
+def test_effective_conductivity_closed_form():
+    """Homogenised x-conductivity of the unit-coefficient TPFA Laplacian on this mesh.
+
+    With transmissibility T_d = 3 on diagonals and 1 on legs, the periodic cell
+    problem gives K = diag(1, T_d/(T_d+2)) in the (1,1),(1,-1) frame, so a
+    walled strip conducts K_xx - K_xy^2/K_yy = T_d/(T_d+1) = 3/4 along x.
+    A wrong |w| on either edge type moves this limit.
+    """
+    got = []
+    for m in (8, 16):
+        tm = mesh.build_mesh(*mesh.square_grid(m))
+        A = ops.weighted_laplacian(tm, np.ones(tm.nedge)).tolil()
+        c = tm.bary
+        b = np.zeros(tm.ncell)
+        left, right = c[:, 0] < 1.0 / m, c[:, 0] > 1 - 1.0 / m
+        b[left] = tm.area[left] / tm.area[left].sum()
+        b[right] = -tm.area[right] / tm.area[right].sum()
+        A[0, :] = 0
+        A[0, 0] = 1
+        b[0] = 0
+        u = spla.spsolve(A.tocsr(), b)
+        mid = (c[:, 0] > 0.25) & (c[:, 0] < 0.75)
+        got.append(-1.0 / np.polyfit(c[mid, 0], u[mid], 1)[0])
+    assert abs(got[1] - 0.75) < abs(got[0] - 0.75) < 0.02
+    assert abs(got[1] - 0.75) < 0.005
+
+
+def test_operator_identities():
+    """div = -grad^T diag(|w||e|), A 1 = 0, J^T M J = M', J^T M 1 = |c'|, P^2 = P, P M'E'^T = 0."""
+    d = ipm.discretise(3, 3)
+    f = d.t.fine
+    D1 = d.div.toarray()
+    D2 = -(d.grad.T @ sp.diags(f.edge_dist * f.edge_len)).toarray()
+    assert np.allclose(D1, D2, atol=1e-14)
+    rng = np.random.default_rng(1)
+    A = ops.weighted_laplacian(f, rng.uniform(0.1, 2, f.nedge))
+    assert np.allclose(A @ np.ones(d.N), 0, atol=1e-13)
+    assert np.allclose((A - A.T).toarray(), 0, atol=1e-14)
+    assert np.allclose((d.J.T @ d.M @ d.J).toarray(), d.Mc.toarray(), atol=1e-16)
+    assert np.allclose(d.J.T @ (d.M @ np.ones(d.N)), d.t.coarse.area)
+    P = d.P_block().toarray()
+    assert np.allclose(P @ P, P, atol=1e-14)
+    mcE = np.kron(np.eye(d.K), d.t.coarse.area[:, None])
+    assert np.allclose(P @ mcE, 0, atol=1e-14)
+    # P^T maps into mass-free vectors: |c'|^T (P^T y)^k = 0
+    y = rng.standard_normal(d.K * d.Nc)
+    z = (P.T @ y).reshape(d.K, d.Nc)
+    assert np.allclose(z @ d.t.coarse.area, 0, atol=1e-15)
+    # R_E is a weighted mean: it preserves constants
+    assert np.allclose(d.RE @ np.ones(d.Nc), 1.0)
+
+
+# ----------------------------------------------------------------- Jacobian
+def _random_state(d, seed=0):
+    rng = np.random.default_rng(seed)
+    phi = rng.standard_normal((d.K + 1) * d.N)
+    rho = rng.uniform(0.5, 2, d.K * d.Nc)
+    s = rng.uniform(0.5, 2, d.K * d.Nc)
+    r0 = rng.uniform(0.5, 2, d.Nc)
+    r1 = rng.uniform(0.5, 2, d.Nc)
+    return phi, rho, s, r0, r1
+
+
+def test_jacobian_matches_central_differences():
+    d = ipm.discretise(2, 2)
+    phi, rho, s, r0, r1 = _random_state(d)
+    Np, Nr = (d.K + 1) * d.N, d.K * d.Nc
+    Jm = ipm.jacobian(d, phi, rho, s, r0, r1).toarray()
+    x = np.concatenate([phi, rho, s])
+    F = lambda x: np.concatenate(ipm.residual(d, x[:Np], x[Np:Np + Nr], x[Np + Nr:], r0, r1, 0.3))  # noqa
+    h = 1e-6
+    FD = np.empty_like(Jm)
+    for i in range(len(x)):
+        e = np.zeros_like(x)
+        e[i] = h
+        FD[:, i] = (F(x + e) - F(x - e)) / (2 * h)
+    assert np.abs(FD - Jm).max() < 1e-7 * np.abs(Jm).max()
+
+
+def test_jacobian_is_symmetric_saddle():
+    """dF_phi/drho equals B^T = (dF_rho/dphi)^T: the Jacobian is a symmetric saddle (Sec. 3)."""
+    d = ipm.discretise(3, 3)
+    phi, rho, s, r0, r1 = _random_state(d, 3)
+    B = d.B_block(phi)
+    assert np.allclose(ipm.dFphi_drho(d, phi).toarray(), B.T.toarray(), atol=1e-13)
+
+
+def test_kernel_of_jacobian_is_global_constant():
+    """Remark (kernel): the Jacobian kernel is spanned by (1, 0, 0)."""
+    d = ipm.discretise(1, 2)
+    phi, rho, s, r0, r1 = _random_state(d, 5)
+    Jm = ipm.jacobian(d, phi, rho, s, r0, r1).toarray()
+    sv = np.linalg.svd(Jm, compute_uv=False)
+    assert sv[-1] < 1e-12 * sv[0] and sv[-2] > 1e-6 * sv[0]
+    Np = (d.K + 1) * d.N
+    e = np.zeros(Jm.shape[0])
+    e[:Np] = 1
+    assert np.abs(Jm @ e).max() < 1e-12
+
+
+# ------------------------------------------------------- projected system
+@pytest.mark.parametrize("n,K", [(1, 1), (2, 2), (2, 3)])
+def test_projected_system_reproduces_newton_direction(n, K):
+    """The projected system (Sec. 4.3.1) plus the per-slice constants of the
+    splitting (reading R10) reproduces the exact Newton direction (dense LU)."""
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(7 + n + K)
+    r0 = rng.uniform(0.5, 2, d.Nc)
+    r1 = rng.uniform(0.5, 2, d.Nc)
+    r1 *= (d.t.coarse.area @ r0) / (d.t.coarse.area @ r1)
+    phi = 0.3 * rng.standard_normal((d.K + 1) * d.N)
+    rho = rng.uniform(0.5, 2, d.K * d.Nc)
+    rho = ipm.renormalise(d, rho, r0)
+    s = rng.uniform(0.5, 2, d.K * d.Nc)
+    mu = 0.1
+    dphi, drho, ds, dropped = ipm.newton_direction(d, phi, rho, s, r0, r1, mu)
+    assert abs(dropped) < 1e-12
+    # dense LU of the full (singular, bordered) Jacobian as an independent route
+    Jm = ipm.jacobian(d, phi, rho, s, r0, r1).toarray()
+    F = np.concatenate(ipm.residual(d, phi, rho, s, r0, r1, mu))
+    Np, Nr = (d.K + 1) * d.N, d.K * d.Nc
+    w = np.zeros(len(F))
+    w[:Np] = np.tile(d.t.fine.area, d.K + 1)
+    e = np.zeros(len(F))
+    e[:Np] = 1
+    big = np.block([[Jm, e[:, None]], [w[None, :], np.zeros((1, 1))]])
+    sol = np.linalg.solve(big, np.concatenate([-F, [0]]))
+    assert np.allclose(sol[:Np], dphi, atol=1e-10)
+    assert np.allclose(sol[Np:Np + Nr], drho, atol=1e-10)
+    assert np.allclose(sol[Np + Nr:-1], ds, atol=1e-10)
+    # projected system
+    f, g, h = -F[:Np], -F[Np:Np + Nr], -F[Np + Nr:]
+    gt = g - np.tile(d.t.coarse.area, d.K) * h / rho
+    Kp = d.projected_kkt(phi, rho, s, r0, r1).toarray()
+    P = d.P_block().toarray()
+    rhs = np.concatenate([f, P @ gt])
+    x = np.linalg.lstsq(Kp, rhs, rcond=None)[0]
+    dphi_hat, drho_p = x[:Np], P.T @ x[Np:]
+    assert np.allclose(drho_p, drho, atol=1e-10)
+    # reading R10: add per-slice constants c^k with |Omega| (c^{k+1}-c^k)/dt = E'_k(g~ - B dphi_hat + C drho)
+    B = d.B_block(phi)
+    C = d.C_block(rho, s)
+    lam = ((gt - B @ dphi_hat + C @ drho_p).reshape(d.K, d.Nc).sum(1)) / d.area_total
+    c = np.concatenate([[0.0], np.cumsum(d.dt * lam)])
+    dphi_rec = (dphi_hat.reshape(d.K + 1, d.N) + c[:, None]).ravel()
+    dphi_rec = ipm.phi_gauge(d, dphi_rec)
+    assert np.allclose(dphi_rec, dphi, atol=1e-9)
+
+
+# ------------------------------------------------------------------- IPM
+def test_uniform_densities_exact_solution():
+    """rho_in = rho_f = c: rho^k = c, s = mu/c, phi^k = -(k-1) dt mu/c + const, C = 0, one Newton step per stage."""
+    n, K, c = 3, 4, 1.0
+    d = ipm.discretise(n, K)
+    r0 = np.full(d.Nc, c)
+    res = ipm.ipm_solve(d, r0, r0.copy(), ipm.IPMOptions(final_newton_tol=1e-12))
+    mu = res.mu
+    assert all(steps == 1 for _, steps, _ in res.stages)
+    assert np.allclose(res.rho, c, rtol=0, atol=1e-13)
+    assert np.allclose(res.s, mu / c, rtol=1e-12)
+    k = np.arange(K + 1)
+    expect = ipm.phi_gauge(d, np.repeat(-k * d.dt * mu / c, d.N))
+    assert np.allclose(res.phi, expect, atol=1e-14)
+    assert abs(res.cost) < 1e-25
+    assert np.isclose(res.cost - res.dual, mu * K / (K + 1), rtol=1e-12)
+
+
+def test_mu_schedule_matches_table3():
+    """mu <- mu/5 from 1 reproduces every row label of Table 3 and stops after ten stages."""
+    labels = [float(x) for x in open(os.path.join(GOLDEN, "mu_schedule_table3.txt")) if x.strip() and x[0] != "#"]
+    opt = ipm.IPMOptions()
+    assert ipm.stage_count(8, opt) == len(labels) == 10
+    mus = [opt.mu0 * opt.mu_factor ** l for l in range(10)]
+    for mu, lab in zip(mus, labels):
+        assert float(f"{mu:.0e}") == lab
+
+
+@pytest.fixture(scope="module")
+def converged_small():
+    n, K = 4, 4
+    d = ipm.discretise(n, K)
+    r0 = make_density(n, [(0.3, 0.3)], [0.1], [1.0], 1e-3)
+    r1 = make_density(n, [(0.7, 0.7)], [0.1], [1.0], 1e-3)
+    res = ipm.ipm_solve(d, r0, r1, ipm.IPMOptions(final_newton_tol=1e-12))
+    return d, r0, r1, res
+
+
+def test_duality_gap_identity(converged_small):
+    """C - D = mu |Omega| K/(K+1) at a solution (summation by parts of F_phi = 0, F_rho = 0, rho s = mu)."""
+    d, r0, r1, res = converged_small
+    gap = res.mu * d.area_total * d.K / (d.K + 1)
+    assert abs((res.cost - res.dual) - gap) < 1e-9 * gap
+    F = ipm.residual(d, res.phi, res.rho, res.s, r0, r1, res.mu)
+    assert ipm.residual_norm(F) < 1e-12
+
+
+def test_mass_positivity_complementarity(converged_small):
+    """Remark one-mass: |c'|^T rho^k = |c'|^T rho^0; rho, s > 0; rho s = mu."""
+    d, r0, r1, res = converged_small
+    R = res.rho.reshape(d.K, d.Nc)
+    assert np.allclose(R @ d.t.coarse.area, d.t.coarse.area @ r0, rtol=0, atol=1e-14)
+    assert res.rho.min() > 0 and res.s.min() > 0
+    assert np.allclose(res.rho * res.s, res.mu, rtol=1e-9)
+    # Newton steps: Sec. 4.1 reports 3-7 per stage and 40-50 in total
+    assert 30 <= res.newton_steps <= 60
+
+
+@pytest.mark.slow
+def test_translation_costs_converge():
+    """Translated equal Gaussians: C -> |d|^2/2 along (1,1), where the scheme's effective
+    metric is exact; C -> (4/3)|d|^2/2 along x, the walled-strip conductivity 3/4 of this mesh."""
+    out = {}
+    for n in (4, 8):
+        d = ipm.discretise(n, n)
+        for name, (c0, c1) in {"diag": ((0.3, 0.3), (0.7, 0.7)), "x": ((0.3, 0.5), (0.7, 0.5))}.items():
+            r0 = make_density(n, [c0], [0.1], [1.0], 1e-3)
+            r1 = make_density(n, [c1], [0.1], [1.0], 1e-3)
+            out[n, name] = ipm.ipm_solve(d, r0, r1).cost
+    e_diag = [abs(out[n, "diag"] / 0.16 - 1) for n in (4, 8)]
+    e_x = [abs(out[n, "x"] / (0.08 * 4 / 3) - 1) for n in (4, 8)]
+    assert e_diag[1] < e_diag[0] < 0.1 and e_diag[1] < 0.03
+    assert e_x[1] < e_x[0] < 0.1 and e_x[1] < 0.03
