@@ -1,0 +1,475 @@
+// k_la.cu -- device memory helpers, reductions and BLAS-1 kernels (FP64).
+//
+// Reductions are deterministic: every block writes its partial result and a
+// second one-block kernel adds the partials in a fixed order.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <chrono>
+#include <cstdio>
+#include <vector>
+
+#include "launch.cuh"
+#include "ot_internal.h"
+
+namespace ot {
+
+static inline cudaStream_t cs(Stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static void cuda_check(cudaError_t e, const char* where) {
+  if (e != cudaSuccess) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    throw Error(e == cudaErrorMemoryAllocation ? 8 : 7, buf);
+  }
+}
+
+namespace prof {
+bool enabled = false;
+unsigned mask = 0;
+long long n_launch = 0;
+namespace {
+struct Pending {
+  int id;
+  cudaEvent_t a, b;
+  double bytes;
+};
+std::vector<cudaEvent_t> pool;
+std::vector<Pending> pending;
+std::vector<cudaEvent_t> open(COUNT, nullptr);
+double ms_acc[COUNT] = {0};
+long long n_acc[COUNT] = {0};
+double b_acc[COUNT] = {0};
+const char* names[COUNT] = {"kkt_apply", "gs_dot", "gs_update", "krylov_combine", "lap_smooth",
+                            "schur_line_smooth", "mg_transfer", "schur_apply", "residual", "bt_apply"};
+cudaEvent_t get_event() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cuda_check(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+}  // namespace
+void begin(int id, Stream s) {
+  if (!enabled || !((mask >> id) & 1u)) return;
+  cudaEvent_t e = get_event();
+  cudaEventRecord(e, cs(s));
+  open[id] = e;
+}
+void end(int id, Stream s, double bytes) {
+  if (!enabled || !open[id]) return;
+  cudaEvent_t e = get_event();
+  cudaEventRecord(e, cs(s));
+  pending.push_back({id, open[id], e, bytes});
+  open[id] = nullptr;
+}
+void harvest() {
+  for (auto& p : pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.b);
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    ms_acc[p.id] += ms;
+    n_acc[p.id] += 1;
+    b_acc[p.id] += p.bytes;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+}
+void reset() {
+  harvest();
+  for (int i = 0; i < COUNT; ++i) ms_acc[i] = 0, n_acc[i] = 0, b_acc[i] = 0;
+}
+const char* name(int id) { return (id >= 0 && id < COUNT) ? names[id] : ""; }
+void read(int id, double* ms, long long* n, double* b) {
+  harvest();
+  *ms = ms_acc[id];
+  *n = n_acc[id];
+  *b = b_acc[id];
+}
+}  // namespace prof
+
+namespace dev {
+void* alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof(buf), "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    throw Error(8, buf);
+  }
+  return p;
+}
+void release(void* p) {
+  if (p) cudaFree(p);
+}
+void* host_alloc(size_t bytes) {
+  void* p = nullptr;
+  cuda_check(cudaMallocHost(&p, bytes ? bytes : 16), "cudaMallocHost");
+  return p;
+}
+void host_release(void* p) {
+  if (p) cudaFreeHost(p);
+}
+void copy_h2d(void* dst, const void* src, size_t bytes, Stream s) {
+  cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs(s)), "cudaMemcpyAsync H2D");
+}
+void copy_d2h(void* dst, const void* src, size_t bytes, Stream s) {
+  cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, cs(s)), "cudaMemcpyAsync D2H");
+}
+void copy_d2d(void* dst, const void* src, size_t bytes, Stream s) {
+  cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, cs(s)), "cudaMemcpyAsync D2D");
+}
+void zero(void* dst, size_t bytes, Stream s) { cuda_check(cudaMemsetAsync(dst, 0, bytes, cs(s)), "cudaMemsetAsync"); }
+void sync(Stream s) {
+  cuda_check(cudaStreamSynchronize(cs(s)), "cudaStreamSynchronize");
+  if (prof::enabled) prof::harvest();
+}
+void check(const char* where) { cuda_check(cudaGetLastError(), where); }
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+double now() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace dev
+
+// ------------------------------------------------------------------ helpers
+static constexpr int kThreads = 256;
+static constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+
+static inline int blocks_for(i64 n, int threads = kThreads, int cap = 1 << 20) {
+  i64 b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+size_t k_reduce_scratch(int nv) { return (size_t)kRedBlocks * (nv + 1) + 64; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v over the block; result valid in thread 0.  smem: blockDim/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? smem[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// out[v] = sum_b partial[b * stride + v], v < nv (one block per v)
+__global__ void k_finish_sum(const double* partial, int nblocks, int stride, int nv, double* out) {
+  __shared__ double sm[32];
+  int v = blockIdx.x;
+  if (v >= nv) return;
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partial[(i64)b * stride + v];
+  a = block_sum(a, sm);
+  if (threadIdx.x == 0) out[v] = a;
+}
+
+// ------------------------------------------------------------------ slice sums
+__global__ void k_slice_sums_kernel(const double* x, i64 n, double scale, double* sums) {
+  __shared__ double sm[32];
+  const double* xs = x + (i64)blockIdx.x * n;
+  double a = 0.0;
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += xs[i];
+  a = block_sum(a, sm);
+  if (threadIdx.x == 0) sums[blockIdx.x] = scale * a;
+}
+
+void k_slice_sums(const double* x, int S, i64 n, double scale, double* sums, Stream s) {
+  launch(k_slice_sums_kernel, S, 512, 0, cs(s), x, n, scale, sums);
+}
+
+__global__ void k_slice_shift_kernel(double* x, int S, i64 n, const double* sums, double scale) {
+  i64 tot = (i64)S * n;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < tot; i += (i64)gridDim.x * blockDim.x)
+    x[i] -= scale * sums[i / n];
+}
+
+void k_slice_shift(double* x, int S, i64 n, const double* sums, double scale, Stream s) {
+  i64 tot = (i64)S * n;
+  launch(k_slice_shift_kernel, blocks_for(tot, kThreads, 4096), kThreads, 0, cs(s), x, S, n, sums, scale);
+}
+
+// ------------------------------------------------------------------ multi-dot (CGS)
+template <int NV>
+__global__ void __launch_bounds__(256) k_mdot_kernel(const double* __restrict__ V, i64 ld, int nv,
+                                                     const double* __restrict__ w, i64 n, double* partial) {
+  __shared__ double sm[NV][8];
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double wi = w[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v < nv) acc[v] += V[(i64)v * ld + i] * wi;
+  }
+  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double t = warp_sum(acc[v]);
+    if (lane == 0) sm[v][wp] = t;
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sm[v][q];
+    partial[(i64)blockIdx.x * (nv + 1) + v] = t;
+  }
+}
+
+template <int NV>
+static void mdot_launch(const double* V, i64 ld, int nv, const double* w, i64 n, double* partial, Stream s) {
+  launch(k_mdot_kernel<NV>, kRedBlocks, 256, 0, cs(s), V, ld, nv, w, n, partial);
+}
+
+void k_mdot(const double* V, i64 ld, int nv, const double* w, i64 n, double* out, double* partial, Stream s) {
+  prof::begin(prof::MDOT, s);
+  int done = 0;
+  while (done < nv) {
+    int c = nv - done;
+    if (c > 32) c = 32;
+    double* pp = partial;
+    if (c <= 8)
+      mdot_launch<8>(V + (i64)done * ld, ld, c, w, n, pp, s);
+    else if (c <= 16)
+      mdot_launch<16>(V + (i64)done * ld, ld, c, w, n, pp, s);
+    else
+      mdot_launch<32>(V + (i64)done * ld, ld, c, w, n, pp, s);
+    launch(k_finish_sum, c, 256, 0, cs(s), pp, kRedBlocks, c + 1, c, out + done);
+    done += c;
+  }
+  prof::end(prof::MDOT, s, 8.0 * (double)(nv + 1) * (double)n);
+}
+
+// w -= sum_v h[v] V_v, then optional dots with the new w and its squared norm.
+template <int NV>
+__global__ void __launch_bounds__(256) k_mupdate_kernel(const double* __restrict__ V, i64 ld, int nv,
+                                                        const double* __restrict__ h, double* w, i64 n,
+                                                        bool dots, bool norm, double* partial) {
+  __shared__ double sm[NV + 1][8];
+  __shared__ double hs[NV];
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) hs[v] = (v < nv) ? h[v] : 0.0;
+  __syncthreads();
+  double acc[NV + 1];
+#pragma unroll
+  for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double vi[NV];
+    double wi = w[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      vi[v] = (v < nv) ? V[(i64)v * ld + i] : 0.0;
+      wi -= hs[v] * vi[v];
+    }
+    w[i] = wi;
+    if (dots) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += vi[v] * wi;
+    }
+    if (norm) acc[NV] += wi * wi;
+  }
+  if (!dots && !norm) return;
+  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v <= NV; ++v) {
+    double t = warp_sum(acc[v]);
+    if (lane == 0) sm[v][wp] = t;
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
+    int src = (v == nv) ? NV : v;
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sm[src][q];
+    partial[(i64)blockIdx.x * (nv + 1) + v] = t;
+  }
+}
+
+void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 n, double* out, bool dots,
+               bool norm, double* partial, Stream s) {
+  prof::begin(prof::MUPDATE, s);
+  struct Closer {
+    Stream s;
+    double b;
+    ~Closer() { prof::end(prof::MUPDATE, s, b); }
+  } closer{s, 8.0 * (double)(nv + 2) * (double)n};
+  if (nv > 32) {
+    // long bases: plain updates in chunks of 32, then separate reductions
+    int done = 0;
+    while (done < nv) {
+      int c = nv - done;
+      if (c > 32) c = 32;
+      launch(k_mupdate_kernel<32>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n, false,
+                                                          false, partial);
+      done += c;
+    }
+    if (dots) k_mdot(V, ld, nv, w, n, out, partial, s);
+    if (norm) k_dot(w, w, n, out + nv, partial, s);
+    return;
+  }
+  if (nv <= 8)
+    launch(k_mupdate_kernel<8>, kRedBlocks, 256, 0, cs(s), V, ld, nv, h, w, n, dots, norm, partial);
+  else if (nv <= 16)
+    launch(k_mupdate_kernel<16>, kRedBlocks, 256, 0, cs(s), V, ld, nv, h, w, n, dots, norm, partial);
+  else
+    launch(k_mupdate_kernel<32>, kRedBlocks, 256, 0, cs(s), V, ld, nv, h, w, n, dots, norm, partial);
+  if (dots) launch(k_finish_sum, nv, 256, 0, cs(s), partial, kRedBlocks, nv + 1, nv, out);
+  if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial + nv, kRedBlocks, nv + 1, 1, out + nv);
+}
+
+__global__ void k_mcombine_kernel(const double* __restrict__ Z, i64 ld, int nv, const double* __restrict__ y,
+                                  double* x, i64 n) {
+  __shared__ double ys[64];
+  for (int v = threadIdx.x; v < nv && v < 64; v += blockDim.x) ys[v] = y[v];
+  __syncthreads();
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double a = x[i];
+    for (int v = 0; v < nv; ++v) a += ys[v] * Z[(i64)v * ld + i];
+    x[i] = a;
+  }
+}
+
+void k_mcombine(const double* Z, i64 ld, int nv, const double* y, double* x, i64 n, Stream s) {
+  prof::begin(prof::MCOMBINE, s);
+  int done = 0;
+  while (done < nv) {
+    int c = nv - done;
+    if (c > 64) c = 64;
+    launch(k_mcombine_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), Z + (i64)done * ld, ld, c,
+                                                                             y + done, x, n);
+    done += c;
+  }
+  prof::end(prof::MCOMBINE, s, 8.0 * (double)(nv + 2) * (double)n);
+}
+
+__global__ void k_dot_kernel(const double* x, const double* y, i64 n, double* partial) {
+  __shared__ double sm[32];
+  double a = 0.0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    a += x[i] * y[i];
+  a = block_sum(a, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
+}
+
+void k_dot(const double* x, const double* y, i64 n, double* out, double* partial, Stream s) {
+  launch(k_dot_kernel, kRedBlocks, kThreads, 0, cs(s), x, y, n, partial);
+  launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out);
+}
+
+__global__ void k_axpby_kernel(double a, const double* x, double b, double* y, i64 n) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+void k_axpby(double a, const double* x, double b, double* y, i64 n, Stream s) {
+  launch(k_axpby_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), a, x, b, y, n);
+}
+
+__global__ void k_scale_inv_norm_kernel(const double* x, const double* nrm2, double* y, i64 n) {
+  double f = 1.0 / sqrt(nrm2[0]);
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+void k_scale_by_inv_norm(const double* x, const double* nrm2, double* y, i64 n, Stream s) {
+  launch(k_scale_inv_norm_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, nrm2, y, n);
+}
+
+__global__ void k_scale_kernel(const double* x, double a, double* y, i64 n) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+void k_scale(const double* x, double a, double* y, i64 n, Stream s) {
+  launch(k_scale_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, a, y, n);
+}
+__global__ void k_fill_kernel(double* x, double v, i64 n) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) x[i] = v;
+}
+void k_fill(double* x, double v, i64 n, Stream s) {
+  launch(k_fill_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, v, n);
+}
+
+// ------------------------------------------------------------------ max |x|, min x
+__global__ void k_absmax_kernel(const double* x, i64 n, double* partial) {
+  __shared__ double sm[32];
+  __shared__ double sb[32];
+  double a = 0.0, bad = 0.0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double v = x[i];
+    if (!isfinite(v)) bad = 1.0;
+    else a = fmax(a, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+    bad = fmax(bad, __shfl_down_sync(0xffffffffu, bad, o));
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sm[w] = a; sb[w] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { a = fmax(a, sm[q]); bad = fmax(bad, sb[q]); }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = bad;
+  }
+}
+__global__ void k_absmax_finish(const double* partial, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, bad = 0.0;
+  for (int b = 0; b < nb; ++b) { a = fmax(a, partial[2 * b]); bad = fmax(bad, partial[2 * b + 1]); }
+  out[0] = a;
+  out[1] = bad;
+}
+void k_absmax(const double* x, i64 n, double* out, double* partial, Stream s) {
+  launch(k_absmax_kernel, kRedBlocks, kThreads, 0, cs(s), x, n, partial);
+  launch(k_absmax_finish, 1, 32, 0, cs(s), partial, kRedBlocks, out);
+}
+
+__global__ void k_min_kernel(const double* x, i64 n, double* partial) {
+  __shared__ double sm[32];
+  double a = INFINITY;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    a = fmin(a, x[i]);
+  for (int o = 16; o > 0; o >>= 1) a = fmin(a, __shfl_down_sync(0xffffffffu, a, o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) a = fmin(a, sm[q]);
+    partial[blockIdx.x] = a;
+  }
+}
+__global__ void k_min_finish(const double* partial, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = INFINITY;
+  for (int b = 0; b < nb; ++b) a = fmin(a, partial[b]);
+  out[0] = a;
+}
+void k_min(const double* x, i64 n, double* out, double* partial, Stream s) {
+  launch(k_min_kernel, kRedBlocks, kThreads, 0, cs(s), x, n, partial);
+  launch(k_min_finish, 1, 32, 0, cs(s), partial, kRedBlocks, out);
+}
+
+}  // namespace ot

@@ -1,0 +1,397 @@
+// k_ops.cu -- FP64 kernels of the discrete operators: residual F, the projected
+// KKT operator, B^T, the BB Schur operator, cost/dual value and the pieces of
+// the Newton update.  One thread per output entry; the bodies are in stencil.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "launch.cuh"
+#include "ot_internal.h"
+
+namespace ot {
+
+static inline cudaStream_t cs(Stream s) { return reinterpret_cast<cudaStream_t>(s); }
+static constexpr int kT = 256;
+static constexpr int kRedBlocks = 608;
+
+static inline int nblk(i64 n) {
+  i64 b = (n + kT - 1) / kT;
+  return (int)(b < 1 ? 1 : b);
+}
+
+#define GRID_LOOP(i, n) for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < (n); i += (i64)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ double warp_sum2(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ residual
+__global__ void k_residual_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0,
+                                      const double* r1, double* F) {
+  i64 tot = (i64)(d.K + 1) * d.N;
+  GRID_LOOP(i, tot) {
+    int jj = (int)(i / d.N);
+    F[i] = residual_phi(d, phi, rho, r0, r1, jj, i - (i64)jj * d.N);
+  }
+}
+
+__global__ void k_residual_rho_kernel(Dims d, double mu, const double* phi, const double* rho, const double* s,
+                                      double* Frho, double* Fs) {
+  i64 tot = (i64)d.K * d.Nc;
+  GRID_LOOP(i, tot) {
+    int k0 = (int)(i / d.Nc);
+    Frho[i] = residual_rho(d, phi, s, k0, i - (i64)k0 * d.Nc);
+    Fs[i] = rho[i] * s[i] - mu;
+  }
+}
+
+void k_residual(const Dims& d, double mu, const double* phi, const double* rho, const double* s,
+                const double* r0, const double* r1, double* Fphi, double* Frho, double* Fs, Stream st) {
+  prof::begin(prof::RESIDUAL, st);
+  launch(k_residual_phi_kernel, nblk((i64)(d.K + 1) * d.N), kT, 0, cs(st), d, phi, rho, r0, r1, Fphi);
+  launch(k_residual_rho_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, mu, phi, rho, s, Frho, Fs);
+  prof::end(prof::RESIDUAL, st, 8.0 * (2.0 * (d.K + 1) * d.N + 4.0 * d.K * d.Nc));
+}
+
+// ------------------------------------------------------------------ KKT operator
+__global__ void k_slice_mean_kernel(const double* x, i64 n, double* mean) {
+  __shared__ double sm[32];
+  const double* xs = x + (i64)blockIdx.x * n;
+  double a = 0.0;
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += xs[i];
+  a = warp_sum2(a);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q];
+    mean[blockIdx.x] = t / (double)n;
+  }
+}
+
+__global__ void k_kkt_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
+                                 const double* xp, const double* xr, const double* xmean, bool with_a, double* y) {
+  i64 tot = (i64)(d.K + 1) * d.N;
+  GRID_LOOP(i, tot) {
+    int jj = (int)(i / d.N);
+    y[i] = kkt_phi(d, phi, rho, r0, r1, xp, xr, xmean, with_a, jj, i - (i64)jj * d.N);
+  }
+}
+
+__global__ void k_kkt_rho_kernel(Dims d, const double* phi, const double* rho, const double* s, const double* xp,
+                                 const double* xr, const double* xmean, double* w) {
+  i64 tot = (i64)d.K * d.Nc;
+  GRID_LOOP(i, tot) {
+    int k0 = (int)(i / d.Nc);
+    w[i] = kkt_rho(d, phi, rho, s, xp, xr, xmean, k0, i - (i64)k0 * d.Nc);
+  }
+}
+
+// y_rho = w - slice mean(w) (P with equal coarse areas); wsum = slice sums of w.
+__global__ void k_project_kernel(double* w, i64 n, double* wsum) {
+  __shared__ double sm[32];
+  __shared__ double mean;
+  double* ws = w + (i64)blockIdx.x * n;
+  double a = 0.0;
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += ws[i];
+  a = warp_sum2(a);
+  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (lane == 0) sm[wp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q];
+    if (wsum) wsum[blockIdx.x] = t;
+    mean = t / (double)n;
+  }
+  __syncthreads();
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) ws[i] -= mean;
+}
+
+void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
+                 const double* r1, const double* x, double* y, double* xmean, double* wsum, Stream st) {
+  i64 Np = (i64)(d.K + 1) * d.N;
+  const double* xr = x + Np;
+  prof::begin(prof::KKT, st);
+  launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
+  launch(k_kkt_phi_kernel, nblk(Np), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
+  launch(k_kkt_rho_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
+  launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, wsum);
+  prof::end(prof::KKT, st, 8.0 * (3.0 * Np + 4.0 * d.K * d.Nc));
+}
+
+void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_phi, double* yr_mean, Stream st) {
+  i64 Np = (i64)(d.K + 1) * d.N;
+  prof::begin(prof::BT, st);
+  launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
+  launch(k_kkt_phi_kernel, nblk(Np), kT, 0, cs(st), d, phi, nullptr, nullptr, nullptr, nullptr, yr, yr_mean, false,
+                                                 out_phi);
+  prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc));
+}
+
+// ------------------------------------------------------------------ Schur operator
+__global__ void k_schur_u_kernel(Dims d, const double* phi, const double* z, double* u) {
+  i64 tot = (i64)(d.K + 1) * d.N;
+  GRID_LOOP(i, tot) {
+    int jj = (int)(i / d.N);
+    u[i] = schur_u(d, phi, z, jj, i - (i64)jj * d.N);
+  }
+}
+
+__global__ void k_schur_out_kernel(Dims d, const double* phi, const double* rho, const double* s, const double* u,
+                                   const double* z, double* out) {
+  i64 tot = (i64)d.K * d.Nc;
+  GRID_LOOP(i, tot) {
+    int k0 = (int)(i / d.Nc);
+    out[i] = schur_out(d, phi, rho, s, u, z, k0, i - (i64)k0 * d.Nc);
+  }
+}
+
+void k_schur_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* z,
+                   double* out, double* u, Stream st) {
+  prof::begin(prof::SCHUR, st);
+  launch(k_schur_u_kernel, nblk((i64)(d.K + 1) * d.N), kT, 0, cs(st), d, phi, z, u);
+  launch(k_schur_out_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rho, s, u, z, out);
+  prof::end(prof::SCHUR, st, 8.0 * ((double)(d.K + 1) * d.N + 4.0 * d.K * d.Nc));
+}
+
+__global__ void k_atilde_kernel(Dims d, const double* rho, const double* z, double* y) {
+  i64 tot = (i64)d.K * d.Nc;
+  GRID_LOOP(i, tot) {
+    int k0 = (int)(i / d.Nc);
+    y[i] = apply_atilde(d, rho, z, k0, i - (i64)k0 * d.Nc) / d.area_c;
+  }
+}
+
+void k_atilde_minv(const Dims& d, const double* rho, const double* z, double* y, Stream st) {
+  launch(k_atilde_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, rho, z, y);
+}
+
+// ------------------------------------------------------------------ cost and dual value
+__global__ void k_cost_dual_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
+                                   double* partial) {
+  __shared__ double sa[32], sb[32];
+  i64 tot = (i64)(d.K + 1) * d.N;
+  double a = 0.0, b = 0.0;
+  GRID_LOOP(i, tot) {
+    int jj = (int)(i / d.N);
+    i64 c = i - (i64)jj * d.N;
+    a += cost_cell(d, phi, rho, r0, r1, jj, c);
+    if (jj == 0) b += dual_cell(d, phi, r0, r1, c);
+  }
+  a = warp_sum2(a);
+  b = warp_sum2(b);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { ta += sa[q]; tb += sb[q]; }
+    partial[2 * blockIdx.x] = ta;
+    partial[2 * blockIdx.x + 1] = tb;
+  }
+}
+
+__global__ void k_cost_dual_finish(const double* partial, int nb, double dt, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int q = 0; q < nb; ++q) { a += partial[2 * q]; b += partial[2 * q + 1]; }
+  out[0] = dt * a;
+  out[1] = b;
+}
+
+void k_cost_dual(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
+                 double* out, double* partial, Stream st) {
+  launch(k_cost_dual_kernel, kRedBlocks, kT, 0, cs(st), d, phi, rho, r0, r1, partial);
+  launch(k_cost_dual_finish, 1, 32, 0, cs(st), partial, kRedBlocks, d.dt, out);
+}
+
+// ------------------------------------------------------------------ Newton pieces
+__global__ void k_newton_rhs_phi(const double* Fphi, double* f, i64 n) {
+  GRID_LOOP(i, n) f[i] = -Fphi[i];
+}
+
+// g~ = -F_rho - |c'| h / rho with h = -(F_s - mu); projected per slice, slice sums kept.
+__global__ void k_newton_rhs_rho(Dims d, const double* Frho, const double* Fs, const double* rho, double* gt,
+                                 double* hvec, double* gsum) {
+  __shared__ double sm[32];
+  __shared__ double mean;
+  i64 base = (i64)blockIdx.x * d.Nc;
+  double a = 0.0;
+  for (i64 i = threadIdx.x; i < d.Nc; i += blockDim.x) {
+    double h = -Fs[base + i];
+    hvec[base + i] = h;
+    double g = -Frho[base + i] - d.area_c * h / rho[base + i];
+    gt[base + i] = g;
+    a += g;
+  }
+  a = warp_sum2(a);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q];
+    gsum[blockIdx.x] = t;
+    mean = t / (double)d.Nc;
+  }
+  __syncthreads();
+  for (i64 i = threadIdx.x; i < d.Nc; i += blockDim.x) gt[base + i] -= mean;
+}
+
+void k_newton_rhs(const Dims& d, const double* Fphi, const double* Frho, const double* Fs, const double* rho,
+                  double* rhs, double* hvec, double* gsum, Stream st) {
+  i64 Np = (i64)(d.K + 1) * d.N;
+  launch(k_newton_rhs_phi, nblk(Np), kT, 0, cs(st), Fphi, rhs, Np);
+  launch(k_newton_rhs_rho, d.K, 512, 0, cs(st), d, Frho, Fs, rho, rhs + Np, hvec, gsum);
+}
+
+// ds = (h - s drho)/rho; candidate step min over negative directions of -x/dx, times tau.
+__global__ void k_step_kernel(i64 n, const double* rho, const double* s, const double* drho, const double* h,
+                              double* ds, double* partial) {
+  __shared__ double sm[32];
+  double a = INFINITY;
+  GRID_LOOP(i, n) {
+    double dsi = (h[i] - s[i] * drho[i]) / rho[i];
+    ds[i] = dsi;
+    if (drho[i] < 0.0) a = fmin(a, -rho[i] / drho[i]);
+    if (dsi < 0.0) a = fmin(a, -s[i] / dsi);
+  }
+  for (int o = 16; o > 0; o >>= 1) a = fmin(a, __shfl_down_sync(0xffffffffu, a, o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) a = fmin(a, sm[q]);
+    partial[blockIdx.x] = a;
+  }
+}
+
+__global__ void k_step_finish(const double* partial, int nb, double tau, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = INFINITY;
+  for (int q = 0; q < nb; ++q) a = fmin(a, partial[q]);
+  out[0] = fmin(1.0, tau * a);
+}
+
+void k_step_length(const Dims& d, const double* rho, const double* s, const double* drho, const double* hvec,
+                   double* ds, double tau, double* out, double* partial, Stream st) {
+  i64 n = (i64)d.K * d.Nc;
+  launch(k_step_kernel, kRedBlocks, kT, 0, cs(st), n, rho, s, drho, hvec, ds, partial);
+  launch(k_step_finish, 1, 32, 0, cs(st), partial, kRedBlocks, tau, out);
+}
+
+__global__ void k_update_kernel(i64 Np, i64 Nr, const double* alpha_dev, double a_host, const double* dphi,
+                                const double* drho, const double* ds, double* phi, double* rho, double* s) {
+  double a = alpha_dev ? alpha_dev[0] : a_host;
+  GRID_LOOP(i, Np) phi[i] += a * dphi[i];
+  GRID_LOOP(i, Nr) {
+    rho[i] += a * drho[i];
+    s[i] += a * ds[i];
+  }
+}
+
+void k_update(const Dims& d, const double* alpha_dev, double a_host, const double* dphi, const double* drho,
+              const double* ds, double* phi, double* rho, double* s, Stream st) {
+  i64 Np = (i64)(d.K + 1) * d.N, Nr = (i64)d.K * d.Nc;
+  launch(k_update_kernel, nblk(Np), kT, 0, cs(st), Np, Nr, alpha_dev, a_host, dphi, drho, ds, phi, rho, s);
+}
+
+__global__ void k_shift_const_kernel(int K, double dt, double area_total, const double* gsum, const double* wsum,
+                                     double* cshift) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double c = 0.0;
+  cshift[0] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    c += dt * (gsum[k] - wsum[k]) / area_total;
+    cshift[k + 1] = c;
+  }
+}
+
+void k_shift_constants(const Dims& d, const double* gsum, const double* wsum, double area_total, double* cshift,
+                       Stream st) {
+  launch(k_shift_const_kernel, 1, 32, 0, cs(st), d.K, d.dt, area_total, gsum, wsum, cshift);
+}
+
+__global__ void k_rescale_kernel(Dims d, double* rho, const double* mass, double target) {
+  i64 tot = (i64)d.K * d.Nc;
+  GRID_LOOP(i, tot) rho[i] *= target / mass[i / d.Nc];
+}
+
+void k_rescale(const Dims& d, double* rho, const double* mass, double target, Stream st) {
+  launch(k_rescale_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, rho, mass, target);
+}
+
+}  // namespace ot
+
+namespace ot {
+// Initial point (reading R8): rho^k = (1 - k dt) rho_in + k dt rho_f, phi = 0, s = mu0 / rho.
+__global__ void k_init_point_kernel(Dims d, double mu0, const double* r0, const double* r1, double* phi,
+                                    double* rho, double* s) {
+  i64 Np = (i64)(d.K + 1) * d.N, Nr = (i64)d.K * d.Nc;
+  GRID_LOOP(i, Np) phi[i] = 0.0;
+  GRID_LOOP(i, Nr) {
+    int k0 = (int)(i / d.Nc);
+    i64 C = i - (i64)k0 * d.Nc;
+    double t = (k0 + 1) * d.dt;
+    double r = (1.0 - t) * r0[C] + t * r1[C];
+    rho[i] = r;
+    s[i] = mu0 / r;
+  }
+}
+
+void k_init_point(const Dims& d, double mu0, const double* r0, const double* r1, double* phi, double* rho,
+                  double* s, Stream st) {
+  launch(k_init_point_kernel, nblk((i64)(d.K + 1) * d.N), kT, 0, cs(st), d, mu0, r0, r1, phi, rho, s);
+}
+
+// out = a .* b * scale
+__global__ void k_mul_kernel(const double* a, const double* b, double scale, double* out, i64 n) {
+  GRID_LOOP(i, n) out[i] = scale * a[i] * b[i];
+}
+void k_mul(const double* a, const double* b, double scale, double* out, i64 n, Stream st) {
+  launch(k_mul_kernel, nblk(n), kT, 0, cs(st), a, b, scale, out, n);
+}
+
+// Adjoint right-hand side dC/du: phi rows dt A^j phi^j, rho rows dt/4 R_T((grad phi^k)^2 + (grad phi^{k+1})^2),
+// the rho rows projected (slice means removed, slice sums to gsum).
+__global__ void k_adj_rhs_phi(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
+                              double* out) {
+  i64 tot = (i64)(d.K + 1) * d.N;
+  GRID_LOOP(i, tot) {
+    int jj = (int)(i / d.N);
+    out[i] = d.dt * lap_apply(d, rho, r0, r1, phi, jj, i - (i64)jj * d.N);
+  }
+}
+
+__global__ void k_adj_rhs_rho(Dims d, const double* phi, double* out) {
+  i64 tot = (i64)d.K * d.Nc;
+  GRID_LOOP(i, tot) {
+    int k0 = (int)(i / d.Nc);
+    i64 C = i - (i64)k0 * d.Nc;
+    out[i] = d.dt * (kinetic_rho(d, phi, k0, C) + kinetic_rho(d, phi, k0 + 1, C));
+  }
+}
+
+void k_adjoint_rhs(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
+                   double* rhs, double* gsum, Stream st) {
+  i64 Np = (i64)(d.K + 1) * d.N;
+  launch(k_adj_rhs_phi, nblk(Np), kT, 0, cs(st), d, phi, rho, r0, r1, rhs);
+  launch(k_adj_rhs_rho, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rhs + Np);
+  launch(k_project_kernel, d.K, 512, 0, cs(st), rhs + Np, d.Nc, gsum);
+}
+
+// grad_in = dt/4 R_T (grad phi^1)^2 - lambda^T dF/drho_in, grad_f likewise with phi^{K+1}.
+__global__ void k_adj_grad_kernel(Dims d, const double* phi, const double* lam, double* gin, double* gf) {
+  GRID_LOOP(C, d.Nc) {
+    gin[C] = d.dt * kinetic_rho(d, phi, 0, C) - adjoint_boundary(d, phi, lam, 0, 1.0, C);
+    gf[C] = d.dt * kinetic_rho(d, phi, d.K, C) - adjoint_boundary(d, phi, lam, d.K, -1.0, C);
+  }
+}
+
+void k_adjoint_grad(const Dims& d, const double* phi, const double* lam, double* gin, double* gf, Stream st) {
+  launch(k_adj_grad_kernel, nblk(d.Nc), kT, 0, cs(st), d, phi, lam, gin, gf);
+}
+}  // namespace ot

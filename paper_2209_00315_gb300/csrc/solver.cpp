@@ -1,0 +1,495 @@
+// solver.cpp -- host orchestration: multigrid cycles, (F)GMRES, the BB
+// preconditioner, Newton directions and the interior-point loop.  Plain C++:
+// device work goes through the launchers of ot_internal.h.
+#include "solver.h"
+
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+#include <vector>
+
+namespace ot {
+
+// ------------------------------------------------------------------ storage
+template <typename T>
+void Hierarchy<T>::build(int m0, int S_, bool tc) {
+  release();
+  S = S_;
+  time_coupled = tc;
+  int m = m0;
+  while (true) {
+    LevelView<T> L;
+    L.m = m;
+    L.nc = 2LL * m * m;
+    size_t v = sizeof(T) * (size_t)S * L.nc;
+    L.alpha = (T*)dev::alloc(3 * v);
+    L.tau = tc ? (T*)dev::alloc(v) : nullptr;
+    L.x = (T*)dev::alloc(v);
+    L.b = (T*)dev::alloc(v);
+    L.r = (T*)dev::alloc(v);
+    lv.push_back(L);
+    if (m % 2 != 0 || m == 1) break;
+    m /= 2;
+  }
+  size_t v0 = sizeof(T) * (size_t)S * lv[0].nc;
+  if (tc) {
+    line_c = (T*)dev::alloc(v0);
+    line_r = (T*)dev::alloc(v0);
+  }
+  agg = (T*)dev::alloc(sizeof(T) * 4 * (size_t)S);
+  acc = (T*)dev::alloc(v0);
+  bsave = (T*)dev::alloc(v0);
+}
+
+template <typename T>
+void Hierarchy<T>::release() {
+  for (auto& L : lv) {
+    dev::release(L.alpha);
+    dev::release(L.tau);
+    dev::release(L.x);
+    dev::release(L.b);
+    dev::release(L.r);
+  }
+  lv.clear();
+  dev::release(line_c);
+  dev::release(line_r);
+  dev::release(agg);
+  dev::release(acc);
+  dev::release(bsave);
+  line_c = line_r = agg = acc = bsave = nullptr;
+}
+
+template struct Hierarchy<float>;
+template struct Hierarchy<double>;
+
+void Krylov::build(int m, i64 n_) {
+  release();
+  mmax = m;
+  n = n_;
+  V = (double*)dev::alloc(sizeof(double) * (size_t)(m + 1) * n);
+  Z = (double*)dev::alloc(sizeof(double) * (size_t)m * n);
+  w = (double*)dev::alloc(sizeof(double) * (size_t)n);
+  hc1 = (double*)dev::alloc(sizeof(double) * (m + 2));
+  hc2 = (double*)dev::alloc(sizeof(double) * (m + 2));
+  y = (double*)dev::alloc(sizeof(double) * (m + 2));
+}
+
+void Krylov::release() {
+  dev::release(V);
+  dev::release(Z);
+  dev::release(w);
+  dev::release(hc1);
+  dev::release(hc2);
+  dev::release(y);
+  V = Z = w = hc1 = hc2 = y = nullptr;
+}
+
+static double* dalloc(i64 n) { return (double*)dev::alloc(sizeof(double) * (size_t)(n > 0 ? n : 1)); }
+
+Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
+  d = make_dims(n, K);
+  precision = prec;
+  Np = (i64)(K + 1) * d.N;
+  Nr = (i64)K * d.Nc;
+  ntot = Np + Nr;
+  try {
+    phi = dalloc(Np);
+    rho = dalloc(Nr);
+    s = dalloc(Nr);
+    r0 = dalloc(d.Nc);
+    r1 = dalloc(d.Nc);
+    Fphi = dalloc(Np);
+    Frho = dalloc(Nr);
+    Fs = dalloc(Nr);
+    rhs = dalloc(ntot);
+    sol = dalloc(ntot);
+    ytmp = dalloc(ntot);
+    hvec = dalloc(Nr);
+    ds = dalloc(Nr);
+    gsum = dalloc(K + 2);
+    wsum = dalloc(K + 2);
+    cshift = dalloc(K + 2);
+    xmean = dalloc(K + 2);
+    mass = dalloc(K + 2);
+    scal = dalloc(64 + 2 * (K + 2));
+    int mm = std::max(opt.fgmres_restart, opt.schur_max_iter) + 2;
+    partial = dalloc((i64)k_reduce_scratch(mm < 64 ? 64 : mm));
+    u = dalloc(Np);
+    bphi = dalloc(Np);
+    srhs = dalloc(Nr);
+    zeta = dalloc(Nr);
+    cur_restart = opt.fgmres_restart;
+    cur_inner = opt.schur_max_iter;
+    outer.build(cur_restart, ntot);
+    inner.build(cur_inner, Nr);
+    if (prec == OT_PREC_MIXED) {
+      lapf.build(d.m, K + 1, false);
+      schf.build(d.n, K, true);
+    } else {
+      lapd.build(d.m, K + 1, false);
+      schd.build(d.n, K, true);
+    }
+    host = (double*)dev::host_alloc(sizeof(double) * 1024);
+  } catch (...) {
+    this->~Workspace();
+    throw;
+  }
+}
+
+Workspace::~Workspace() {
+  double* bufs[] = {phi, rho, s, r0, r1, Fphi, Frho, Fs, rhs, sol, ytmp, hvec, ds, gsum, wsum, cshift, xmean,
+                    mass, scal, partial, u, bphi, srhs, zeta};
+  for (double* b : bufs) dev::release(b);
+  phi = rho = s = r0 = r1 = Fphi = Frho = Fs = rhs = sol = ytmp = hvec = ds = nullptr;
+  gsum = wsum = cshift = xmean = mass = scal = partial = u = bphi = srhs = zeta = nullptr;
+  outer.release();
+  inner.release();
+  lapf.release();
+  schf.release();
+  lapd.release();
+  schd.release();
+  dev::host_release(host);
+  host = nullptr;
+}
+
+// ------------------------------------------------------------------ multigrid
+template <typename T>
+static void vcycle(Hierarchy<T>& H, size_t l, int nu, int nuc, Stream st) {
+  LevelView<T>& L = H.lv[l];
+  if (l + 1 == H.lv.size()) {
+    k_mg_coarse_solve<T>(H.S, L, nuc, H.line_c, H.line_r, H.agg, st);
+    return;
+  }
+  dev::zero(L.x, sizeof(T) * (size_t)H.S * L.nc, st);
+  for (int i = 0; i < nu; ++i) {
+    k_mg_smooth<T>(H.S, L, 0, H.line_c, H.line_r, st);
+    k_mg_smooth<T>(H.S, L, 1, H.line_c, H.line_r, st);
+  }
+  k_mg_residual<T>(H.S, L, st);
+  k_mg_restrict<T>(H.S, L, H.lv[l + 1], st);
+  vcycle(H, l + 1, nu, nuc, st);
+  k_mg_prolong<T>(H.S, H.lv[l + 1], L, st);
+  for (int i = 0; i < nu; ++i) {
+    k_mg_smooth<T>(H.S, L, 1, H.line_c, H.line_r, st);
+    k_mg_smooth<T>(H.S, L, 0, H.line_c, H.line_r, st);
+  }
+}
+
+// x ~= M^{-1} b by `cycles` V-cycles from zero (b, x in FP64; the cycle in T).
+template <typename T>
+static void mg_solve(Hierarchy<T>& H, const double* b, double* x, int cycles, int nu, int nuc, Stream st) {
+  LevelView<T>& L = H.lv[0];
+  i64 n = (i64)H.S * L.nc;
+  size_t bytes = sizeof(T) * (size_t)n;
+  k_mg_load<T>(b, 1.0, L.b, nullptr, n, st);
+  if (cycles <= 1) {
+    vcycle(H, 0, nu, nuc, st);
+    k_mg_store<T>(L.x, x, n, st);
+    return;
+  }
+  dev::copy_d2d(H.bsave, L.b, bytes, st);
+  vcycle(H, 0, nu, nuc, st);
+  dev::copy_d2d(H.acc, L.x, bytes, st);
+  for (int c = 1; c < cycles; ++c) {
+    dev::copy_d2d(L.x, H.acc, bytes, st);
+    dev::copy_d2d(L.b, H.bsave, bytes, st);
+    k_mg_residual<T>(H.S, L, st);
+    dev::copy_d2d(L.b, L.r, bytes, st);
+    vcycle(H, 0, nu, nuc, st);
+    k_mg_axpy<T>(L.x, (T)1, H.acc, n, st);
+  }
+  k_mg_store<T>(H.acc, x, n, st);
+}
+
+template <typename T>
+static void refresh_t(Workspace& W, Hierarchy<T>& lap, Hierarchy<T>& sch, Stream st) {
+  k_mg_lap_coef0<T>(W.d, W.rho, W.r0, W.r1, lap.lv[0].alpha, st);
+  for (size_t l = 0; l + 1 < lap.lv.size(); ++l) k_mg_restrict_coef<T>(lap.S, lap.lv[l], lap.lv[l + 1], st);
+  k_mg_schur_coef0<T>(W.d, W.rho, W.s, sch.lv[0].alpha, sch.lv[0].tau, st);
+  for (size_t l = 0; l + 1 < sch.lv.size(); ++l) k_mg_restrict_coef<T>(sch.S, sch.lv[l], sch.lv[l + 1], st);
+}
+
+void refresh_coefficients(Workspace& W, Stream st) {
+  if (W.precision == OT_PREC_MIXED)
+    refresh_t(W, W.lapf, W.schf, st);
+  else
+    refresh_t(W, W.lapd, W.schd, st);
+}
+
+// ------------------------------------------------------------------ Arnoldi
+typedef std::function<void(const double*, double*)> OpFn;
+
+// One restart cycle of right-preconditioned flexible GMRES.  K.V[0] holds the
+// normalised residual, beta its norm.  Classical Gram-Schmidt with one
+// reorthogonalisation on the device; Givens rotations on the host.  On return
+// x += Z y and *res is the residual estimate; returns the number of steps.
+static int arnoldi(Workspace& W, Krylov& K, int m, double beta, double tol_abs, const OpFn& prec, const OpFn& op,
+                   double* x, double* res, Stream st) {
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 1.0), sn(m, 0.0), g(m + 1, 0.0);
+  auto h = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
+  g[0] = beta;
+  double r = beta;
+  int j = 0;
+  double* hb = W.host;
+  for (j = 0; j < m;) {
+    double* vj = K.V + (i64)j * K.n;
+    double* zj = K.Z + (i64)j * K.n;
+    prec(vj, zj);
+    op(zj, K.w);
+    k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
+    k_mupdate(K.V, K.n, j + 1, K.hc1, K.w, K.n, K.hc2, true, false, W.partial, st);
+    k_mupdate(K.V, K.n, j + 1, K.hc2, K.w, K.n, K.hc2, false, true, W.partial, st);
+    k_scale_by_inv_norm(K.w, K.hc2 + j + 1, K.V + (i64)(j + 1) * K.n, K.n, st);
+    dev::copy_d2h(hb, K.hc1, sizeof(double) * (j + 1), st);
+    dev::copy_d2h(hb + 512, K.hc2, sizeof(double) * (j + 2), st);
+    dev::sync(st);
+    for (int i = 0; i <= j; ++i) h(i, j) = hb[i] + hb[512 + i];
+    double hn = sqrt(std::max(hb[512 + j + 1], 0.0));
+    h(j + 1, j) = hn;
+    for (int i = 0; i < j; ++i) {
+      double a = h(i, j), b = h(i + 1, j);
+      h(i, j) = cs[i] * a + sn[i] * b;
+      h(i + 1, j) = -sn[i] * a + cs[i] * b;
+    }
+    double a = h(j, j), b = h(j + 1, j);
+    double den = hypot(a, b);
+    cs[j] = den > 0 ? a / den : 1.0;
+    sn[j] = den > 0 ? b / den : 0.0;
+    h(j, j) = den;
+    h(j + 1, j) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    r = fabs(g[j + 1]);
+    if (!isfinite(r)) throw Error(OT_ERR_NONFINITE, "non-finite value in the Krylov iteration");
+    ++j;
+    if (r <= tol_abs || hn <= 1e-14 * beta) break;
+  }
+  int k = j;
+  std::vector<double> y(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int q = i + 1; q < k; ++q) t -= h(i, q) * y[q];
+    y[i] = (h(i, i) != 0.0) ? t / h(i, i) : 0.0;
+  }
+  dev::copy_h2d(K.y, y.data(), sizeof(double) * k, st);
+  k_mcombine(K.Z, K.n, k, K.y, x, K.n, st);
+  dev::sync(st);  // y lives on the host stack
+  *res = r;
+  return k;
+}
+
+static double norm2(Workspace& W, const double* x, i64 n, Stream st) {
+  k_dot(x, x, n, W.scal + 32, W.partial, st);
+  dev::copy_d2h(W.host + 1000, W.scal + 32, sizeof(double), st);
+  dev::sync(st);
+  return sqrt(std::max(W.host[1000], 0.0));
+}
+
+// ------------------------------------------------------------------ BB preconditioner
+template <typename T>
+static void inner_solve(Workspace& W, const ot_options& opt, Hierarchy<T>& sch, const double* b, double* x,
+                        Stream st) {
+  Krylov& K = W.inner;
+  i64 n = W.Nr;
+  dev::zero(x, sizeof(double) * (size_t)n, st);
+  double beta = norm2(W, b, n, st);
+  if (beta == 0.0) return;
+  k_scale(b, 1.0 / beta, K.V, n, st);
+  OpFn prec = [&](const double* in, double* out) {
+    mg_solve(sch, in, out, 1, opt.smooth_sweeps, opt.coarse_sweeps, st);
+  };
+  OpFn op = [&](const double* in, double* out) { k_schur_apply(W.d, W.phi, W.rho, W.s, in, out, W.u, st); };
+  double res = 0.0;
+  int its = arnoldi(W, K, std::min(opt.schur_max_iter, K.mmax), beta, opt.eps_schur * beta, prec, op, x, &res, st);
+  W.inner_iters += its;
+}
+
+template <typename T>
+static void bb_apply_t(Workspace& W, const ot_options& opt, Hierarchy<T>& lap, Hierarchy<T>& sch, const double* v,
+                       double* out, Stream st) {
+  const Dims& d = W.d;
+  const double* c = v;
+  const double* dv = v + W.Np;
+  double* x = out;
+  double* y = out + W.Np;
+  // Schur system (Eq. pseudoschur-bis): (Diag(s) A~ - Diag(rho) B M^-1 B~) z = -Diag(rho) d
+  k_mul(W.rho, dv, -1.0, W.srhs, W.Nr, st);
+  inner_solve(W, opt, sch, W.srhs, W.zeta, st);
+  // y = M'^{-1} A~ z
+  k_atilde_minv(d, W.rho, W.zeta, y, st);
+  // b = c - B^T P^T y, kept in the range of A (zero slice sums)
+  k_bt_apply(d, W.phi, y, W.bphi, W.xmean, st);
+  k_axpby(1.0, c, -1.0, W.bphi, W.Np, st);
+  double* sm = W.scal + 64;
+  k_slice_sums(W.bphi, d.K + 1, d.N, 1.0 / (double)d.N, sm, st);
+  k_slice_shift(W.bphi, d.K + 1, d.N, sm, 1.0, st);
+  // A^j x^j = b^j, j = 1..K+1, by multigrid (Eq. x-triang)
+  mg_solve(lap, W.bphi, x, opt.lap_cycles, opt.smooth_sweeps, opt.coarse_sweeps, st);
+}
+
+void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st) {
+  if (W.precision == OT_PREC_MIXED)
+    bb_apply_t(W, opt, W.lapf, W.schf, v, out, st);
+  else
+    bb_apply_t(W, opt, W.lapd, W.schd, v, out, st);
+}
+
+// ------------------------------------------------------------------ FGMRES
+double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, double tol_abs, Stream st) {
+  Krylov& K = W.outer;
+  i64 n = W.ntot;
+  dev::zero(x, sizeof(double) * (size_t)n, st);
+  double beta = norm2(W, b, n, st);
+  if (beta <= tol_abs) return beta;
+  k_scale(b, 1.0 / beta, K.V, n, st);
+  OpFn prec = [&](const double* in, double* out) { bb_apply(W, opt, in, out, st); };
+  OpFn op = [&](const double* in, double* out) {
+    k_kkt_apply(W.d, W.phi, W.rho, W.s, W.r0, W.r1, in, out, W.xmean, nullptr, st);
+  };
+  int total = 0;
+  double res = beta;
+  while (true) {
+    int m = std::min(std::min(opt.fgmres_restart, K.mmax), opt.fgmres_max_iter - total);
+    if (m <= 0) break;
+    total += arnoldi(W, K, m, beta, tol_abs, prec, op, x, &res, st);
+    if (res <= tol_abs || total >= opt.fgmres_max_iter) break;
+    // restart from the true residual
+    op(x, K.w);
+    dev::copy_d2d(K.V, b, sizeof(double) * (size_t)n, st);
+    k_axpby(-1.0, K.w, 1.0, K.V, n, st);
+    beta = norm2(W, K.V, n, st);
+    res = beta;
+    if (beta <= tol_abs) break;
+    k_scale(K.V, 1.0 / beta, K.V, n, st);
+  }
+  W.outer_iters += total;
+  if (res > tol_abs) W.capped_solves++;
+  return res;
+}
+
+// ------------------------------------------------------------------ Newton
+double residual_norm(Workspace& W, double mu, Stream st, double* norms) {
+  k_residual(W.d, mu, W.phi, W.rho, W.s, W.r0, W.r1, W.Fphi, W.Frho, W.Fs, st);
+  k_dot(W.Fphi, W.Fphi, W.Np, W.scal + 0, W.partial, st);
+  k_dot(W.Frho, W.Frho, W.Nr, W.scal + 1, W.partial, st);
+  k_dot(W.Fs, W.Fs, W.Nr, W.scal + 2, W.partial, st);
+  dev::copy_d2h(W.host, W.scal, 3 * sizeof(double), st);
+  dev::sync(st);
+  double t = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    if (!isfinite(W.host[i])) throw Error(OT_ERR_NONFINITE, "non-finite residual");
+    if (norms) norms[i] = sqrt(W.host[i]);
+    t += W.host[i];
+  }
+  return sqrt(t);
+}
+
+// Recover the full direction from the projected solution in W.sol (reading R10):
+// drho <- P^T drho, dphi <- dphi_hat + per-slice constants, zero mean.
+void recover_direction(Workspace& W, Stream st) {
+  const Dims& d = W.d;
+  double* dphi = W.sol;
+  double* drho = W.sol + W.Np;
+  double* sm = W.scal + 64;
+  k_slice_sums(drho, d.K, d.Nc, 1.0 / (double)d.Nc, sm, st);
+  k_slice_shift(drho, d.K, d.Nc, sm, 1.0, st);
+  k_kkt_apply(d, W.phi, W.rho, W.s, W.r0, W.r1, W.sol, W.ytmp, W.xmean, W.wsum, st);
+  k_shift_constants(d, W.gsum, W.wsum, 1.0, W.cshift, st);
+  k_slice_shift(dphi, d.K + 1, d.N, W.cshift, -1.0, st);
+  k_slice_sums(dphi, 1, W.Np, 1.0 / (double)W.Np, sm, st);
+  k_slice_shift(dphi, 1, W.Np, sm, 1.0, st);
+}
+
+double newton_direction(Workspace& W, const ot_options& opt, double normF, double eps, Stream st) {
+  const Dims& d = W.d;
+  k_newton_rhs(d, W.Fphi, W.Frho, W.Fs, W.rho, W.rhs, W.hvec, W.gsum, st);
+  refresh_coefficients(W, st);
+  fgmres(W, opt, W.rhs, W.sol, eps * normF, st);
+  recover_direction(W, st);
+  k_step_length(d, W.rho, W.s, W.sol + W.Np, W.hvec, W.ds, opt.tau, W.scal + 8, W.partial, st);
+  dev::copy_d2h(W.host, W.scal + 8, sizeof(double), st);
+  dev::sync(st);
+  return W.host[0];
+}
+
+// ------------------------------------------------------------------ interior point
+int ipm_run(Workspace& W, const ot_options& opt, double mu0, double tol, ot_stats* stats, Stream st) {
+  const Dims& d = W.d;
+  const int K = d.K;
+  const double area_total = 1.0;
+  int n_stage = 1;
+  {
+    double mu = mu0;
+    while (mu * area_total * K / (K + 1.0) > tol && n_stage < OT_MAX_STAGES) {
+      mu *= opt.mu_factor;
+      ++n_stage;
+    }
+  }
+  k_slice_sums(W.r0, 1, d.Nc, d.area_c, W.scal + 16, st);
+  dev::copy_d2h(W.host, W.scal + 16, sizeof(double), st);
+  dev::sync(st);
+  const double mass0 = W.host[0];
+
+  double t_start = dev::now();
+  double mu = mu0;
+  double f = 0.0;
+  int total_newton = 0;
+  W.outer_iters = W.inner_iters = W.capped_solves = 0;
+  for (int stage = 0; stage < n_stage; ++stage) {
+    double t0 = dev::now();
+    long long o0 = W.outer_iters, i0 = W.inner_iters;
+    double norms[3];
+    f = residual_norm(W, mu, st, norms);
+    bool last = stage == n_stage - 1;
+    double tolN = ((last && opt.final_newton_tol > 0) ? opt.final_newton_tol : opt.newton_tol) * std::max(1.0, f);
+    double eps = (last && opt.final_eps_out > 0) ? opt.final_eps_out : opt.eps_out;
+    int steps = 0;
+    while (f > tolN) {
+      if (steps >= opt.max_newton) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "Newton did not converge at mu=%g: ||F||=%.3e after %d steps", mu, f, steps);
+        throw Error(OT_ERR_NOT_CONVERGED, buf);
+      }
+      double alpha = newton_direction(W, opt, f, eps, st);
+      if (!(alpha > 0.0) || !isfinite(alpha)) throw Error(OT_ERR_BREAKDOWN, "zero or invalid step length");
+      k_update(d, W.scal + 8, 0.0, W.sol, W.sol + W.Np, W.ds, W.phi, W.rho, W.s, st);
+      k_slice_sums(W.rho, K, d.Nc, d.area_c, W.mass, st);
+      k_rescale(d, W.rho, W.mass, mass0, st);
+      f = residual_norm(W, mu, st, norms);
+      ++steps;
+      if (opt.verbose >= 2)
+        fprintf(stderr, "  newton %2d  mu=%.2e  alpha=%.3f  ||F||=%.3e  outer=%lld inner=%lld\n", steps, mu, alpha,
+                f, W.outer_iters - o0, W.inner_iters - i0);
+    }
+    total_newton += steps;
+    double t1 = dev::now();
+    if (opt.verbose >= 1)
+      fprintf(stderr, "stage %2d mu=%.2e newton=%d outer/ls=%.1f inner/outer=%.2f ||F||=%.3e %.3fs\n", stage, mu,
+              steps, steps ? (double)(W.outer_iters - o0) / steps : 0.0,
+              (W.outer_iters - o0) ? (double)(W.inner_iters - i0) / (double)(W.outer_iters - o0) : 0.0, f, t1 - t0);
+    if (stats && stage < OT_MAX_STAGES) {
+      stats->stage_mu[stage] = mu;
+      stats->stage_newton[stage] = steps;
+      stats->stage_outer[stage] = W.outer_iters - o0;
+      stats->stage_inner[stage] = W.inner_iters - i0;
+      stats->stage_seconds[stage] = t1 - t0;
+      stats->stage_residual[stage] = f;
+    }
+    if (!last) mu *= opt.mu_factor;
+  }
+  if (stats) {
+    stats->stages = n_stage;
+    stats->newton_steps = total_newton;
+    stats->fgmres_iters = W.outer_iters;
+    stats->inner_iters = W.inner_iters;
+    stats->final_residual = f;
+    stats->mu = mu;
+    stats->gap = mu * area_total * K / (K + 1.0);
+    stats->seconds = dev::now() - t_start;
+  }
+  return total_newton;
+}
+
+}  // namespace ot

@@ -1,0 +1,84 @@
+// solver.h -- workspace and host orchestration of the IPM / FGMRES / BB path.
+#pragma once
+#include <vector>
+
+#include "../../include/ot.h"
+#include "ot_internal.h"
+
+namespace ot {
+
+// Multigrid hierarchy on nested grids of sides m0, m0/2, ... (down to an odd side).
+template <typename T>
+struct Hierarchy {
+  int S = 0;               // slices
+  bool time_coupled = false;
+  std::vector<LevelView<T>> lv;
+  T* line_c = nullptr;     // Thomas scratch, S x nc(level 0)
+  T* line_r = nullptr;
+  T* agg = nullptr;        // 4 S
+  T* acc = nullptr;        // level-0 accumulator for repeated cycles
+  T* bsave = nullptr;      // level-0 right-hand side for repeated cycles
+  void build(int m0, int S, bool time_coupled);
+  void release();
+  bool built() const { return !lv.empty(); }
+};
+
+// Krylov basis storage for one (F)GMRES solver.
+struct Krylov {
+  int mmax = 0;
+  i64 n = 0;
+  double* V = nullptr;     // (mmax+1) x n
+  double* Z = nullptr;     // mmax x n
+  double* w = nullptr;     // n
+  double* hc1 = nullptr;   // mmax+2
+  double* hc2 = nullptr;   // mmax+2
+  double* y = nullptr;     // mmax
+  void build(int m, i64 n);
+  void release();
+};
+
+// Everything one (mesh, K, precision) needs on the device.
+struct Workspace {
+  Dims d;
+  int precision = OT_PREC_FP64;
+  i64 Np = 0, Nr = 0, ntot = 0;
+  // state
+  double *phi = nullptr, *rho = nullptr, *s = nullptr, *r0 = nullptr, *r1 = nullptr;
+  // residual and Newton
+  double *Fphi = nullptr, *Frho = nullptr, *Fs = nullptr;
+  double *rhs = nullptr, *sol = nullptr, *hvec = nullptr, *ds = nullptr, *ytmp = nullptr;
+  double *gsum = nullptr, *wsum = nullptr, *cshift = nullptr, *xmean = nullptr, *mass = nullptr;
+  double* scal = nullptr;     // 64 device scalars
+  double* partial = nullptr;  // reduction scratch
+  // BB
+  double *u = nullptr, *bphi = nullptr, *srhs = nullptr, *zeta = nullptr;
+  Krylov outer, inner;
+  Hierarchy<float> lapf, schf;
+  Hierarchy<double> lapd, schd;
+  double* host = nullptr;     // pinned host scratch (256 doubles)
+  // counters of the current call
+  long long outer_iters = 0, inner_iters = 0, capped_solves = 0;
+  int cur_restart = 0, cur_inner = 0;
+
+  Workspace(int n, int K, int precision, const ot_options& opt);
+  ~Workspace();
+};
+
+// Level-0 coefficients of both hierarchies and their coarsenings from the current (rho, s).
+void refresh_coefficients(Workspace& W, Stream st);
+// One BB preconditioner application (Sec. 4.3): out = P_BB^{-1} v, both of length ntot.
+void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st);
+// FGMRES on the projected system; x (ntot) receives the solution; returns the final residual estimate.
+double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, double tol_abs, Stream st);
+// Residual at the state in W for parameter mu; returns ||F|| (norms[0..2]: component norms).
+double residual_norm(Workspace& W, double mu, Stream st, double* norms);
+// Newton direction at the state in W; requires the residual of that state in W.F*.
+// On return: sol = (dphi; drho), ds, and scal[0] = step length (device); returns the step length.
+double newton_direction(Workspace& W, const ot_options& opt, double normF, double eps, Stream st);
+// Turn the projected solution in W.sol into the full direction (reading R10):
+// drho <- P^T drho; dphi <- dphi_hat + per-slice constants from W.gsum; zero mean.
+void recover_direction(Workspace& W, Stream st);
+// Full interior-point solve from the state in W (initialised by the caller).
+int ipm_run(Workspace& W, const ot_options& opt, double mu0, double tol, ot_stats* stats, Stream st);
+
+}  // namespace ot

@@ -1,0 +1,465 @@
+// stencil.cuh -- per-element bodies of every stencil of the path.
+//
+// Each function computes one output entry from plain pointers; the CUDA
+// kernels call them once per thread.  All geometry is arithmetic on the
+// structured right-triangle grids:
+//
+//   grid of side m: squares (I, J), 0 <= I, J < m, side h = 1/m; square (I, J)
+//   holds the lower-right triangle L = (t=0) and the upper-left U = (t=1),
+//   cell index t m^2 + J m + I, area h^2/2.
+//   Interior edges and their two-point transmissibility |e|/|w|:
+//     diagonal of (I,J): L(I,J) | U(I,J)      |e| = sqrt2 h, |w| = sqrt2 h/3 -> 3
+//     right of (I,J):    L(I,J) | U(I+1,J)    |e| = h, |w| = h            -> 1
+//     top of (I,J):      U(I,J) | L(I,J+1)    |e| = h, |w| = h            -> 1
+//   (|w| on the diagonals is the barycentre distance: the circumcentres of the
+//   two right triangles coincide there.)  Every cell has three edge slots:
+//     L: 0 -> U(I,J), 1 -> U(I+1,J), 2 -> U(I,J-1)
+//     U: 0 -> L(I,J), 1 -> L(I-1,J), 2 -> L(I,J+1)
+//   and the mesh graph is bipartite: every neighbour of an L cell is a U cell.
+//
+//   Two levels (Sec. 2.1): the fine grid (side 2n, potential) is the midpoint
+//   4-split of the coarse grid (side n, density).  Fine square (I, J) lies in
+//   coarse square (I/2, J/2); of its two triangles, only the upper-left one of
+//   sub-square (0,1) and the lower-right one of sub-square (1,0) belong to the
+//   other coarse triangle than their type says.
+//
+//   All edge reconstructions use weight 1/2 on each side (lambda_e = 1/2 on this
+//   mesh), so R_E rho on a fine edge is the mean of the two parents' values and
+//   W_e (grad u)_e (grad v)_e = T_e (u_c - u_o)(v_c - v_o) for |e||w| = W_e.
+#pragma once
+#include <stdint.h>
+
+#ifndef OT_HD
+#ifdef __CUDACC__
+#define OT_HD __host__ __device__ __forceinline__
+#else
+#define OT_HD inline
+#endif
+#endif
+
+namespace ot {
+
+typedef long long i64;
+
+// Sizes of one problem: coarse side n, fine side m = 2n, K density slices.
+struct Dims {
+  int n, m, K;
+  i64 N, Nc;            // fine / coarse cells per slice
+  double dt;            // 1/(K+1)
+  double area_f, area_c;
+};
+
+OT_HD Dims make_dims(int n, int K) {
+  Dims d;
+  d.n = n;
+  d.m = 2 * n;
+  d.K = K;
+  d.Nc = 2LL * n * n;
+  d.N = 2LL * d.m * d.m;
+  d.dt = 1.0 / (K + 1);
+  d.area_c = 0.5 / ((double)n * n);
+  d.area_f = 0.5 / ((double)d.m * d.m);
+  return d;
+}
+
+OT_HD double trans(int slot) { return slot == 0 ? 3.0 : 1.0; }
+
+struct Cell {
+  int t, I, J;
+};
+
+OT_HD Cell decode(int m, i64 c) {
+  Cell q;
+  i64 mm = (i64)m * m;
+  q.t = (int)(c / mm);
+  i64 r = c - (i64)q.t * mm;
+  q.J = (int)(r / m);
+  q.I = (int)(r - (i64)q.J * m);
+  return q;
+}
+
+OT_HD i64 encode(int m, int t, int I, int J) { return (i64)t * m * m + (i64)J * m + I; }
+
+// Neighbour of each edge slot, -1 on the domain boundary (no-flux edges are dropped).
+OT_HD void neighbours(int m, const Cell& q, i64 nb[3]) {
+  if (q.t == 0) {
+    nb[0] = encode(m, 1, q.I, q.J);
+    nb[1] = (q.I + 1 < m) ? encode(m, 1, q.I + 1, q.J) : -1;
+    nb[2] = (q.J > 0) ? encode(m, 1, q.I, q.J - 1) : -1;
+  } else {
+    nb[0] = encode(m, 0, q.I, q.J);
+    nb[1] = (q.I > 0) ? encode(m, 0, q.I - 1, q.J) : -1;
+    nb[2] = (q.J + 1 < m) ? encode(m, 0, q.I, q.J + 1) : -1;
+  }
+}
+
+// Coarse triangle (grid side m/2) containing fine cell q (grid side m): the injection J.
+OT_HD i64 parent(int m, const Cell& q) {
+  int n = m >> 1;
+  int a = q.I & 1, b = q.J & 1;
+  int tc = (q.t == 0) ? ((a == 0 && b == 1) ? 1 : 0) : ((a == 1 && b == 0) ? 0 : 1);
+  return encode(n, tc, q.I >> 1, q.J >> 1);
+}
+
+OT_HD i64 parent_of(int m, i64 c) { return parent(m, decode(m, c)); }
+
+// The four fine cells (grid side 2n) of coarse cell q (grid side n).
+OT_HD void children(int n, const Cell& q, i64 ch[4]) {
+  int m = 2 * n, I = 2 * q.I, J = 2 * q.J;
+  if (q.t == 0) {
+    ch[0] = encode(m, 0, I, J);
+    ch[1] = encode(m, 0, I + 1, J + 1);
+    ch[2] = encode(m, 0, I + 1, J);
+    ch[3] = encode(m, 1, I + 1, J);
+  } else {
+    ch[0] = encode(m, 1, I, J);
+    ch[1] = encode(m, 1, I + 1, J + 1);
+    ch[2] = encode(m, 0, I, J + 1);
+    ch[3] = encode(m, 1, I, J + 1);
+  }
+}
+
+// rho^k for k = 0..K+1 (paper index): boundary data at k = 0 and k = K+1.
+OT_HD double rho_at(const Dims& d, const double* rho, const double* r0, const double* r1, int k, i64 C) {
+  return k == 0 ? r0[C] : (k == d.K + 1 ? r1[C] : rho[(i64)(k - 1) * d.Nc + C]);
+}
+
+// Mean density of phi slice jj (paper j = jj+1) on coarse cell C: (rho^{j-1} + rho^j)/2.
+OT_HD double rho_bar(const Dims& d, const double* rho, const double* r0, const double* r1, int jj, i64 C) {
+  return 0.5 * (rho_at(d, rho, r0, r1, jj, C) + rho_at(d, rho, r0, r1, jj + 1, C));
+}
+
+// ----------------------------------------------------------------- residual
+// F_phi^j on fine cell c, phi slice jj = j-1 (Eq. conservation_discrete):
+//   -|c| (rho^j - rho^{j-1})_P/dt + sum_e T_e rho~^j_e (phi_c - phi_o).
+OT_HD double residual_phi(const Dims& d, const double* phi, const double* rho, const double* r0,
+                          const double* r1, int jj, i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  i64 P = parent(d.m, q);
+  const double* ph = phi + (i64)jj * d.N;
+  double ra = rho_at(d, rho, r0, r1, jj, P), rb = rho_at(d, rho, r0, r1, jj + 1, P);
+  double rc = 0.5 * (ra + rb);
+  double acc = -d.area_f * (rb - ra) / d.dt;
+  double pc = ph[c];
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    double ro = rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]));
+    acc += trans(sl) * 0.5 * (rc + ro) * (pc - ph[nb[sl]]);
+  }
+  return acc;
+}
+
+// F_rho^k on coarse cell C, rho slice k0 = k-1 (Eq. hj_discrete, time term J^T M):
+//   sum_{c in C} [ |c| (phi^{k+1} - phi^k)_c/dt + 1/8 sum_e T_e ((dphi^k_e)^2 + (dphi^{k+1}_e)^2) ] + |c'| s^k_C.
+// (R_T q = 1/2 sum_{c in C} sum_{e at c} W_e q_e counts interior fine edges twice at 1/2.)
+OT_HD double residual_rho(const Dims& d, const double* phi, const double* s, int k0, i64 C) {
+  Cell qc = decode(d.n, C);
+  i64 ch[4];
+  children(d.n, qc, ch);
+  const double* p0 = phi + (i64)k0 * d.N;
+  const double* p1 = p0 + d.N;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    i64 c = ch[a];
+    Cell q = decode(d.m, c);
+    i64 nb[3];
+    neighbours(d.m, q, nb);
+    acc += d.area_f * (p1[c] - p0[c]) / d.dt;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      if (nb[sl] < 0) continue;
+      double g0 = p0[c] - p0[nb[sl]], g1 = p1[c] - p1[nb[sl]];
+      acc += 0.125 * trans(sl) * (g0 * g0 + g1 * g1);
+    }
+  }
+  return acc + d.area_c * s[(i64)k0 * d.Nc + C];
+}
+
+// ----------------------------------------------------------------- KKT operator
+// phi rows of [A, B^T P^T] x, phi slice jj (paper j = jj+1), with y = P^T x_rho (slice means xmean removed):
+//   sum_e T_e [rho~^j_e (x_c - x_o) + (ybar^j_Pc + ybar^j_Po)/2 (phi_c - phi_o)] + |c| (y^{j-1} - y^j)_Pc/dt,
+//   ybar^j = (y^{j-1} + y^j)/2, y^0 = y^{K+1} = 0.  with_a = false drops the A term.
+OT_HD double kkt_phi(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
+                     const double* xp, const double* xr, const double* xmean, bool with_a, int jj, i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  i64 P = parent(d.m, q);
+  const double* ph = phi + (i64)jj * d.N;
+  const double* xs = xp + (i64)jj * d.N;
+  const double* ym = (jj >= 1) ? xr + (i64)(jj - 1) * d.Nc : nullptr;
+  const double* yp = (jj <= d.K - 1) ? xr + (i64)jj * d.Nc : nullptr;
+  double mm = (jj >= 1) ? xmean[jj - 1] : 0.0, mp = (jj <= d.K - 1) ? xmean[jj] : 0.0;
+  double yma = ym ? ym[P] - mm : 0.0, ypa = yp ? yp[P] - mp : 0.0;
+  double acc = d.area_f * (yma - ypa) / d.dt;
+  double ybc = 0.5 * (yma + ypa);
+  double rc = with_a ? rho_bar(d, rho, r0, r1, jj, P) : 0.0;
+  double pc = ph[c], xc = with_a ? xs[c] : 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    i64 o = nb[sl];
+    i64 Po = parent_of(d.m, o);
+    double ybo = 0.5 * ((ym ? ym[Po] - mm : 0.0) + (yp ? yp[Po] - mp : 0.0));
+    double term = 0.5 * (ybc + ybo) * (pc - ph[o]);
+    if (with_a) term += 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, Po)) * (xc - xs[o]);
+    acc += trans(sl) * term;
+  }
+  return acc;
+}
+
+// (B x)^k on coarse cell C, rho slice k0 = k-1 (Sec. 3, B = J^T D_t M + H G D_x):
+//   sum_{c in C} [ |c| (x^{k+1} - x^k)_c/dt
+//                  + 1/4 sum_e T_e ((phi^k_c - phi^k_o)(x^k_c - x^k_o) + (same at k+1)) ].
+OT_HD double apply_B(const Dims& d, const double* phi, const double* x, int k0, i64 C) {
+  Cell qc = decode(d.n, C);
+  i64 ch[4];
+  children(d.n, qc, ch);
+  const double* p0 = phi + (i64)k0 * d.N;
+  const double* p1 = p0 + d.N;
+  const double* x0 = x + (i64)k0 * d.N;
+  const double* x1 = x0 + d.N;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    i64 c = ch[a];
+    Cell q = decode(d.m, c);
+    i64 nb[3];
+    neighbours(d.m, q, nb);
+    acc += d.area_f * (x1[c] - x0[c]) / d.dt;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      if (nb[sl] < 0) continue;
+      i64 o = nb[sl];
+      acc += 0.25 * trans(sl) * ((p0[c] - p0[o]) * (x0[c] - x0[o]) + (p1[c] - p1[o]) * (x1[c] - x1[o]));
+    }
+  }
+  return acc;
+}
+
+// rho rows before projection: w = B x_phi - C P^T x_rho, C = M' diag(s/rho).
+OT_HD double kkt_rho(const Dims& d, const double* phi, const double* rho, const double* s, const double* xp,
+                     const double* xr, const double* xmean, int k0, i64 C) {
+  i64 idx = (i64)k0 * d.Nc + C;
+  double xh = xr[idx] - xmean[k0];
+  return apply_B(d, phi, xp, k0, C) - d.area_c * s[idx] / rho[idx] * xh;
+}
+
+// ----------------------------------------------------------------- BB pieces
+// u = M^{-1} B~ z on fine cell c, phi slice jj (paper j = jj+1), reading of Sec. 4.3.2:
+//   (z^j - z^{j-1})_Pc/dt + 1/(2|c|) sum_e T_e (phi^j_c - phi^j_o)(zbar^j_Pc - zbar^j_Po),
+//   zbar^j = (z^{j-1} + z^j)/2, z^0 = z^{K+1} = 0.
+OT_HD double schur_u(const Dims& d, const double* phi, const double* z, int jj, i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  i64 P = parent(d.m, q);
+  const double* ph = phi + (i64)jj * d.N;
+  const double* zm = (jj >= 1) ? z + (i64)(jj - 1) * d.Nc : nullptr;
+  const double* zp = (jj <= d.K - 1) ? z + (i64)jj * d.Nc : nullptr;
+  double zmc = zm ? zm[P] : 0.0, zpc = zp ? zp[P] : 0.0;
+  double zbc = 0.5 * (zmc + zpc);
+  double acc = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    i64 Po = parent_of(d.m, nb[sl]);
+    double zbo = 0.5 * ((zm ? zm[Po] : 0.0) + (zp ? zp[Po] : 0.0));
+    acc += trans(sl) * (ph[c] - ph[nb[sl]]) * (zbc - zbo);
+  }
+  return (zpc - zmc) / d.dt + 0.5 * acc / d.area_f;
+}
+
+// (A~^k z)_C on the coarse grid: sum_E T_E (rho^k_C + rho^k_O)/2 (z_C - z_O).
+OT_HD double apply_atilde(const Dims& d, const double* rho, const double* z, int k0, i64 C) {
+  Cell q = decode(d.n, C);
+  i64 nb[3];
+  neighbours(d.n, q, nb);
+  const double* rk = rho + (i64)k0 * d.Nc;
+  const double* zk = z + (i64)k0 * d.Nc;
+  double acc = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    acc += trans(sl) * 0.5 * (rk[C] + rk[nb[sl]]) * (zk[C] - zk[nb[sl]]);
+  }
+  return acc;
+}
+
+// Schur operator row (Eq. pseudoschur-bis): s (A~ z) - rho (B u) with u = M^{-1} B~ z.
+OT_HD double schur_out(const Dims& d, const double* phi, const double* rho, const double* s, const double* u,
+                       const double* z, int k0, i64 C) {
+  i64 idx = (i64)k0 * d.Nc + C;
+  return s[idx] * apply_atilde(d, rho, z, k0, C) - rho[idx] * apply_B(d, phi, u, k0, C);
+}
+
+// ----------------------------------------------------------------- cost, dual
+// Contribution of fine cell c, phi slice jj, to sum_e W rho~ (grad phi)^2 / 2: each edge is
+// visited from both sides, so the cell adds 1/4 sum_e T_e rho~_e (phi_c - phi_o)^2.
+OT_HD double cost_cell(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
+                       int jj, i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  i64 P = parent(d.m, q);
+  const double* ph = phi + (i64)jj * d.N;
+  double rc = rho_bar(d, rho, r0, r1, jj, P);
+  double acc = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    double g = ph[c] - ph[nb[sl]];
+    acc += trans(sl) * 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]))) * g * g;
+  }
+  return 0.25 * acc;
+}
+
+// Contribution of fine cell c to the dual value D:
+//   |c| (phi^{K+1}_c rho_f,Pc - phi^1_c rho_in,Pc)
+//   - dt/4 * 1/2 sum_e T_e [R_E rho_in]_e (dphi^1_e)^2 + [R_E rho_f]_e (dphi^{K+1}_e)^2.
+OT_HD double dual_cell(const Dims& d, const double* phi, const double* r0, const double* r1, i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  i64 P = parent(d.m, q);
+  const double* pa = phi;
+  const double* pb = phi + (i64)d.K * d.N;
+  double acc = d.area_f * (pb[c] * r1[P] - pa[c] * r0[P]);
+  double corr = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    i64 o = nb[sl], Po = parent_of(d.m, o);
+    double ga = pa[c] - pa[o], gb = pb[c] - pb[o];
+    corr += trans(sl) * (0.5 * (r0[P] + r0[Po]) * ga * ga + 0.5 * (r1[P] + r1[Po]) * gb * gb);
+  }
+  return acc - 0.25 * d.dt * 0.5 * corr;
+}
+
+// ----------------------------------------------------------------- adjoint
+// (A^j x^j)_c = sum_e T_e rho~^j_e (x_c - x_o), phi slice jj.
+OT_HD double lap_apply(const Dims& d, const double* rho, const double* r0, const double* r1, const double* x, int jj,
+                       i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  const double* xs = x + (i64)jj * d.N;
+  double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
+  double acc = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    acc += trans(sl) * 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]))) * (xs[c] - xs[nb[sl]]);
+  }
+  return acc;
+}
+
+// 1/4 (R_T (grad phi^a)^2)_C = 1/8 sum_{c in C} sum_e T_e (dphi^a_e)^2 for phi slice ja.
+OT_HD double kinetic_rho(const Dims& d, const double* phi, int ja, i64 C) {
+  Cell qc = decode(d.n, C);
+  i64 ch[4];
+  children(d.n, qc, ch);
+  const double* p = phi + (i64)ja * d.N;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    i64 c = ch[a];
+    i64 nb[3];
+    neighbours(d.m, decode(d.m, c), nb);
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      if (nb[sl] < 0) continue;
+      double g = p[c] - p[nb[sl]];
+      acc += 0.125 * trans(sl) * g * g;
+    }
+  }
+  return acc;
+}
+
+// lambda^T dF_phi^{ja+1}/d(boundary density) on coarse cell C, for ja = 0 (rho_in, sign = +1)
+// or ja = K (rho_f, sign = -1):
+//   sum_{c in C} [ sign |c| lambda_c / dt + 1/4 sum_e T_e (phi_c - phi_o)(lambda_c - lambda_o) ].
+OT_HD double adjoint_boundary(const Dims& d, const double* phi, const double* lam, int ja, double sign, i64 C) {
+  Cell qc = decode(d.n, C);
+  i64 ch[4];
+  children(d.n, qc, ch);
+  const double* p = phi + (i64)ja * d.N;
+  const double* l = lam + (i64)ja * d.N;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    i64 c = ch[a];
+    i64 nb[3];
+    neighbours(d.m, decode(d.m, c), nb);
+    acc += sign * d.area_f * l[c] / d.dt;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      if (nb[sl] < 0) continue;
+      acc += 0.25 * trans(sl) * (p[c] - p[nb[sl]]) * (l[c] - l[nb[sl]]);
+    }
+  }
+  return acc;
+}
+
+// ----------------------------------------------------------------- multigrid
+// Level operators have, per (slice, cell), three row coefficients alpha[slot]
+// (spatial couplings alpha (x_c - x_o)) and, for the space-time Schur
+// hierarchy, a time coefficient tau coupling the cell to itself at k-1, k+1:
+//   (M x)^k_c = sum_slot alpha^k_{c,slot} (x^k_c - x^k_o) + tau^k_c (2 x^k_c - x^{k-1}_c - x^{k+1}_c),
+// with x^{-1} = x^K = 0 (Dirichlet in time).  Coefficients are stored
+// [slot][slice][cell].
+
+// Level-0 coefficients of the slice Laplacian A^j: T_e rho~^j_e.
+OT_HD double lap_coef(const Dims& d, const double* rho, const double* r0, const double* r1, int jj, i64 c,
+                      int sl) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  if (nb[sl] < 0) return 0.0;
+  double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
+  double ro = rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]));
+  return trans(sl) * 0.5 * (rc + ro);
+}
+
+// Level-0 coefficients of the simplified Schur operator on the coarse grid:
+//   alpha = s^k_C T_E (rho^k_C + rho^k_O)/2  (the Diag(s) A~ part),
+//   tau   = rho^k_C |c'| / dt^2              (the time part of -Diag(rho) B M^{-1} B~).
+OT_HD double schur_coef(const Dims& d, const double* rho, const double* s, int k0, i64 C, int sl) {
+  Cell q = decode(d.n, C);
+  i64 nb[3];
+  neighbours(d.n, q, nb);
+  if (nb[sl] < 0) return 0.0;
+  const double* rk = rho + (i64)k0 * d.Nc;
+  return s[(i64)k0 * d.Nc + C] * trans(sl) * 0.5 * (rk[C] + rk[nb[sl]]);
+}
+
+OT_HD double schur_tau(const Dims& d, const double* rho, int k0, i64 C) {
+  return rho[(i64)k0 * d.Nc + C] * d.area_c / (d.dt * d.dt);
+}
+
+// Coarse coefficient from the fine level (side m -> m/2): the Galerkin sum of
+// the two fine edges making up each coarse edge, halved for the spatial
+// (second-order) part; tau is summed over the four children.
+//   coarse L(i,j): slot0 <- L(2i,2j).0, L(2i+1,2j+1).0; slot1 <- L(2i+1,2j).1, L(2i+1,2j+1).1;
+//                  slot2 <- L(2i,2j).2, L(2i+1,2j).2
+//   coarse U(i,j): slot0 <- U(2i,2j).0, U(2i+1,2j+1).0; slot1 <- U(2i,2j).1, U(2i,2j+1).1;
+//                  slot2 <- U(2i,2j+1).2, U(2i+1,2j+1).2
+OT_HD void coarse_coef_sources(int mc, i64 C, int sl, i64 src[2]) {
+  Cell q = decode(mc, C);
+  int m = 2 * mc, I = 2 * q.I, J = 2 * q.J;
+  if (q.t == 0) {
+    if (sl == 0) { src[0] = encode(m, 0, I, J); src[1] = encode(m, 0, I + 1, J + 1); }
+    else if (sl == 1) { src[0] = encode(m, 0, I + 1, J); src[1] = encode(m, 0, I + 1, J + 1); }
+    else { src[0] = encode(m, 0, I, J); src[1] = encode(m, 0, I + 1, J); }
+  } else {
+    if (sl == 0) { src[0] = encode(m, 1, I, J); src[1] = encode(m, 1, I + 1, J + 1); }
+    else if (sl == 1) { src[0] = encode(m, 1, I, J); src[1] = encode(m, 1, I, J + 1); }
+    else { src[0] = encode(m, 1, I, J + 1); src[1] = encode(m, 1, I + 1, J + 1); }
+  }
+}
+
+}  // namespace ot
