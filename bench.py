@@ -32,6 +32,7 @@ WORKLOAD_DESC = ("64x64 squares -> 8192 coarse / 32768 fine triangles, K=32, 3-G
                  "(centres U[0.15,0.85]^2, sigma U[0.05,0.15], weights U[0.5,1.5], seeds 2/3), floor 1e-4, "
                  "unit mass, mu0=1, mu <- mu/5, stop at duality gap 1e-6")
 SAMPLE_N, SAMPLE_K = 12, 6   # bounded sample of the same density recipe for the CPU oracle
+SAMPLE_EVERY = 16            # time one launch in 16 of the roofline kernel inside the timed region
 METRIC = "IPM time-to-solution at duality gap 1e-6"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in profiles/ (None if the
 # kernel changed since it was taken)
@@ -169,7 +170,7 @@ def run_ours(args, world, rank, local):
             capi.ot_ipm_solve(mesh, r0d, r1d, K, options=opt)
         barrier()
         if groups is not None:
-            capi.ot_kernel_timing_enable(groups)
+            capi.ot_kernel_timing_enable(groups, sample_every=SAMPLE_EVERY)
         launches0 = capi.ot_kernel_launches()
         ms, res = [], None
         for _ in range(steps):

@@ -203,8 +203,9 @@ ot_status ot_cost_dual(ot_mesh* mesh, int32_t K, const double* phi, const double
  * ---------------------------------------------------------------------- */
 
 /* Turn the accounting on for the groups whose bit is set in group_mask (bit i =
- * group i; -1 = all, 0 = off); every call resets the counters. */
-void ot_kernel_timing_enable(int32_t group_mask);
+ * group i; -1 = all, 0 = off), timing one launch in `sample_every` (>= 1) of
+ * each group; every call resets the counters. */
+void ot_kernel_timing_enable(int32_t group_mask, int32_t sample_every);
 
 /* Number of instrumented kernel groups. */
 int32_t ot_kernel_timing_count(void);

@@ -100,7 +100,7 @@ def load():
         "ot_schur_apply": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
         "ot_bb_apply": (_I, [_P, _I, C.POINTER(ot_options), _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_cost_dual": (_I, [_P, _I, _P, _P, _P, _P, C.POINTER(_D), C.POINTER(_D), _P]),
-        "ot_kernel_timing_enable": (None, [_I]),
+        "ot_kernel_timing_enable": (None, [_I, _I]),
         "ot_kernel_timing_count": (_I, []),
         "ot_kernel_launches": (C.c_int64, []),
         "ot_kernel_timing_read": (_I, [_I, C.POINTER(C.c_char_p), C.POINTER(_D), C.POINTER(C.c_int64),
@@ -289,8 +289,9 @@ def ot_kernel_timing_groups() -> list:
     return names
 
 
-def ot_kernel_timing_enable(groups=True) -> None:
-    """groups: True (all), False (off), or an iterable of group names."""
+def ot_kernel_timing_enable(groups=True, sample_every: int = 1) -> None:
+    """groups: True (all), False (off), or an iterable of group names; one launch in
+    ``sample_every`` of each group is timed."""
     if groups is True:
         mask = -1
     elif groups is False or groups is None:
@@ -300,7 +301,7 @@ def ot_kernel_timing_enable(groups=True) -> None:
         mask = 0
         for g in groups:
             mask |= 1 << names.index(g)
-    load().ot_kernel_timing_enable(int(mask))
+    load().ot_kernel_timing_enable(int(mask), int(sample_every))
 
 
 def ot_kernel_timing_read() -> dict:

@@ -67,7 +67,7 @@ void ot_default_options(ot_options* o) {
   o->schur_max_iter = 20;
   o->lap_cycles = 2;     // two V(2,2) cycles: ~5e-2 relative residual, the paper's Laplacian tolerance
   o->smooth_sweeps = 2;
-  o->coarse_sweeps = 20;
+  o->coarse_sweeps = 6;
   o->max_newton = 50;
   o->verbose = 0;
 }
@@ -392,9 +392,10 @@ ot_status ot_bb_apply(ot_mesh* mesh, int32_t K, const ot_options* opt_in, const 
   OT_CATCH
 }
 
-void ot_kernel_timing_enable(int32_t group_mask) {
+void ot_kernel_timing_enable(int32_t group_mask, int32_t sample_every) {
   ot::prof::reset();
   ot::prof::mask = (unsigned)group_mask;
+  ot::prof::stride = sample_every > 1 ? sample_every : 1;
   ot::prof::enabled = group_mask != 0;
 }
 

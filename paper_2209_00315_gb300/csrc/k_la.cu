@@ -28,7 +28,9 @@ namespace prof {
 bool enabled = false;
 unsigned mask = 0;
 long long n_launch = 0;
+int stride = 1;
 namespace {
+unsigned long long seen[COUNT] = {0};
 struct Pending {
   int id;
   cudaEvent_t a, b;
@@ -55,6 +57,7 @@ cudaEvent_t get_event() {
 }  // namespace
 void begin(int id, Stream s) {
   if (!enabled || !((mask >> id) & 1u)) return;
+  if (++seen[id] % (unsigned long long)stride != 0) return;
   cudaEvent_t e = get_event();
   cudaEventRecord(e, cs(s));
   open[id] = e;
@@ -81,7 +84,7 @@ void harvest() {
 }
 void reset() {
   harvest();
-  for (int i = 0; i < COUNT; ++i) ms_acc[i] = 0, n_acc[i] = 0, b_acc[i] = 0;
+  for (int i = 0; i < COUNT; ++i) ms_acc[i] = 0, n_acc[i] = 0, b_acc[i] = 0, seen[i] = 0;
 }
 const char* name(int id) { return (id >= 0 && id < COUNT) ? names[id] : ""; }
 void read(int id, double* ms, long long* n, double* b) {

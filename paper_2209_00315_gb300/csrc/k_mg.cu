@@ -46,21 +46,24 @@ void k_mg_lap_coef0(const Dims& d, const double* rho, const double* r0, const do
 }
 
 template <typename T>
-__global__ void k_schur_coef0_kernel(Dims d, const double* rho, const double* s, T* alpha, T* tau) {
+__global__ void k_schur_coef0_kernel(Dims d, const double* phi, const double* rho, const double* s, T* alpha,
+                                     T* tau) {
   int S = d.K;
   i64 tot = (i64)S * d.Nc;
   GRID_LOOP(i, tot) {
     int k0 = (int)(i / d.Nc);
     i64 C = i - (i64)k0 * d.Nc;
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl) alpha[((i64)sl * S + k0) * d.Nc + C] = (T)schur_coef(d, rho, s, k0, C, sl);
+    for (int sl = 0; sl < 3; ++sl)
+      alpha[((i64)sl * S + k0) * d.Nc + C] = (T)schur_coef(d, phi, rho, s, k0, C, sl);
     tau[i] = (T)schur_tau(d, rho, k0, C);
   }
 }
 
 template <typename T>
-void k_mg_schur_coef0(const Dims& d, const double* rho, const double* s, T* alpha, T* tau, Stream st) {
-  launch(k_schur_coef0_kernel<T>, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, rho, s, alpha, tau);
+void k_mg_schur_coef0(const Dims& d, const double* phi, const double* rho, const double* s, T* alpha, T* tau,
+                      Stream st) {
+  launch(k_schur_coef0_kernel<T>, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rho, s, alpha, tau);
 }
 
 // ------------------------------------------------------------------ coarse coefficients
@@ -109,15 +112,143 @@ __global__ void k_line_smooth_kernel(int S, LevelView<T> L, int color, T* lc, T*
   GRID_LOOP(i, sq) line_gs(S, L, (i64)color * sq + i, lc, lr);
 }
 
+// ---- warp line solves: parallel cyclic reduction along time.
+// A warp owns one cell's time line; lane l holds slices l, l+32, ... (KPL per
+// lane, padded with identity equations to 32 KPL), and log2(32 KPL)
+// elimination steps replace the K dependent steps of a Thomas sweep.
+// Row k: a_k x_{k-s} + d_k x_k + c_k x_{k+s} = r_k at stride s.
+template <typename T, int KPL>
+__device__ __forceinline__ void pcr_solve(T (&a)[KPL], T (&d)[KPL], T (&c)[KPL], T (&r)[KPL], int lane) {
+  constexpr int LOG2 = (KPL == 1) ? 5 : (KPL == 2) ? 6 : 7;
+#pragma unroll
+  for (int j = 0; j < LOG2; ++j) {
+    const int s = 1 << j;
+    T am[KPL], dm[KPL], cm[KPL], rm[KPL], ap[KPL], dp[KPL], cp[KPL], rp[KPL];
+    if (s < 32) {
+      const int lm = (lane - s) & 31, lp = (lane + s) & 31;
+      T xa[KPL], xd[KPL], xc[KPL], xr[KPL], ya[KPL], yd[KPL], yc[KPL], yr[KPL];
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        xa[q] = __shfl_sync(0xffffffffu, a[q], lm);
+        xd[q] = __shfl_sync(0xffffffffu, d[q], lm);
+        xc[q] = __shfl_sync(0xffffffffu, c[q], lm);
+        xr[q] = __shfl_sync(0xffffffffu, r[q], lm);
+        ya[q] = __shfl_sync(0xffffffffu, a[q], lp);
+        yd[q] = __shfl_sync(0xffffffffu, d[q], lp);
+        yc[q] = __shfl_sync(0xffffffffu, c[q], lp);
+        yr[q] = __shfl_sync(0xffffffffu, r[q], lp);
+      }
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        if (lane >= s) {
+          am[q] = xa[q]; dm[q] = xd[q]; cm[q] = xc[q]; rm[q] = xr[q];
+        } else if (q >= 1) {
+          am[q] = xa[q - 1]; dm[q] = xd[q - 1]; cm[q] = xc[q - 1]; rm[q] = xr[q - 1];
+        } else {
+          am[q] = 0; dm[q] = 1; cm[q] = 0; rm[q] = 0;
+        }
+        if (lane + s < 32) {
+          ap[q] = ya[q]; dp[q] = yd[q]; cp[q] = yc[q]; rp[q] = yr[q];
+        } else if (q + 1 < KPL) {
+          ap[q] = ya[q + 1]; dp[q] = yd[q + 1]; cp[q] = yc[q + 1]; rp[q] = yr[q + 1];
+        } else {
+          ap[q] = 0; dp[q] = 1; cp[q] = 0; rp[q] = 0;
+        }
+      }
+    } else {
+      const int t = s >> 5;
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        if (q - t >= 0) {
+          am[q] = a[q - t]; dm[q] = d[q - t]; cm[q] = c[q - t]; rm[q] = r[q - t];
+        } else {
+          am[q] = 0; dm[q] = 1; cm[q] = 0; rm[q] = 0;
+        }
+        if (q + t < KPL) {
+          ap[q] = a[q + t]; dp[q] = d[q + t]; cp[q] = c[q + t]; rp[q] = r[q + t];
+        } else {
+          ap[q] = 0; dp[q] = 1; cp[q] = 0; rp[q] = 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      T al = -a[q] / dm[q], ga = -c[q] / dp[q];
+      T nd = d[q] + al * cm[q] + ga * ap[q];
+      T nr = r[q] + al * rm[q] + ga * rp[q];
+      a[q] = al * am[q];
+      c[q] = ga * cp[q];
+      d[q] = nd;
+      r[q] = nr;
+    }
+  }
+}
+
+// Line update of cell c (same system as line_gs) by one warp.
+template <typename T, int KPL>
+__device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, int lane) {
+  i64 nb[3];
+  neighbours(L.m, decode(L.m, c), nb);
+  T a[KPL], d[KPL], cc[KPL], r[KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    int k = lane + 32 * q;
+    if (k < S) {
+      i64 o = (i64)k * L.nc;
+      T tau = L.tau[o + c];
+      T dg = 2 * tau, rhs = L.b[o + c];
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        T al = L.alpha[((i64)sl * S + k) * L.nc + c];
+        dg += al;
+        if (nb[sl] >= 0) rhs += al * L.x[o + nb[sl]];
+      }
+      d[q] = dg;
+      r[q] = rhs;
+      a[q] = (k > 0) ? -tau : (T)0;
+      cc[q] = (k < S - 1) ? -tau : (T)0;
+    } else {
+      d[q] = 1; r[q] = 0; a[q] = 0; cc[q] = 0;
+    }
+  }
+  pcr_solve<T, KPL>(a, d, cc, r, lane);
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    int k = lane + 32 * q;
+    if (k < S) L.x[(i64)k * L.nc + c] = r[q] / d[q];
+  }
+}
+
+template <typename T, int KPL>
+__global__ void __launch_bounds__(256) k_line_pcr_kernel(int S, LevelView<T> L, int color) {
+  i64 sq = (i64)L.m * L.m;
+  int lane = threadIdx.x & 31;
+  i64 w0 = (blockIdx.x * (i64)blockDim.x + threadIdx.x) >> 5;
+  i64 nw = ((i64)gridDim.x * blockDim.x) >> 5;
+  for (i64 w = w0; w < sq; w += nw) line_pcr<T, KPL>(S, L, (i64)color * sq + w, lane);
+}
+
+static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128 ? 4 : 0)); }
+
 template <typename T>
 void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, Stream st) {
   i64 sq = (i64)L.m * L.m;
   int id = L.tau ? prof::SCH_SMOOTH : prof::LAP_SMOOTH;
   prof::begin(id, st);
-  if (L.tau)
-    launch(k_line_smooth_kernel<T>, nblk(sq), kT, 0, cs(st), S, L, color, line_c, line_r);
-  else
+  if (L.tau) {
+    int kpl = pcr_kpl(S);
+    int blocks = (int)std::min<i64>((sq * 32 + kT - 1) / kT, 1 << 20);
+    if (kpl == 1)
+      launch(k_line_pcr_kernel<T, 1>, blocks, kT, 0, cs(st), S, L, color);
+    else if (kpl == 2)
+      launch(k_line_pcr_kernel<T, 2>, blocks, kT, 0, cs(st), S, L, color);
+    else if (kpl == 4)
+      launch(k_line_pcr_kernel<T, 4>, blocks, kT, 0, cs(st), S, L, color);
+    else
+      launch(k_line_smooth_kernel<T>, nblk(sq), kT, 0, cs(st), S, L, color, line_c, line_r);
+  } else {
     launch(k_point_smooth_kernel<T>, nblk((i64)S * sq), kT, 0, cs(st), S, L, color);
+  }
   // per updated cell: b, three coefficients, the neighbours' x, the new x (+ tau for lines)
   prof::end(id, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)sq);
 }
@@ -177,17 +308,21 @@ void k_mg_prolong(int S, const LevelView<T>& coarse, const LevelView<T>& fine, S
 // the correction on the single aggregate of all cells (the Galerkin operator
 // on the constant-per-slice space is the time-tridiagonal tau_G (2 d^k - d^{k-1} - d^{k+1}),
 // tau_G = sum of tau over the cells), followed by `sweeps` more sweeps.
-template <typename T>
+// KPL > 0: time lines and the aggregate system by warp PCR; KPL = 0: Thomas per thread.
+template <typename T, int KPL>
 __global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, int sweeps, T* lc, T* lr, T* agg) {
   i64 sq = (i64)L.m * L.m;
   i64 tot = (i64)S * L.nc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (i64 i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] = 0;
   __syncthreads();
   int passes = L.tau ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
     for (int it = 0; it < sweeps; ++it) {
       for (int color = 0; color < 2; ++color) {
-        if (L.tau) {
+        if (L.tau && KPL > 0) {
+          for (i64 w = warp; w < sq; w += nwarp) line_pcr<T, (KPL > 0 ? KPL : 1)>(S, L, (i64)color * sq + w, lane);
+        } else if (L.tau) {
           for (i64 i = threadIdx.x; i < sq; i += blockDim.x) line_gs(S, L, (i64)color * sq + i, lc, lr);
         } else {
           for (i64 i = threadIdx.x; i < (i64)S * sq; i += blockDim.x) {
@@ -216,7 +351,31 @@ __global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, i
       agg[S + k] = tsum;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (KPL > 0) {
+      constexpr int Q = KPL > 0 ? KPL : 1;
+      if (warp == 0) {
+        T a[Q], d[Q], c[Q], r[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          int k = lane + 32 * q;
+          if (k < S) {
+            T tg = agg[S + k];
+            d[q] = 2 * tg;
+            r[q] = agg[k];
+            a[q] = (k > 0) ? -tg : (T)0;
+            c[q] = (k < S - 1) ? -tg : (T)0;
+          } else {
+            d[q] = 1; r[q] = 0; a[q] = 0; c[q] = 0;
+          }
+        }
+        pcr_solve<T, Q>(a, d, c, r, lane);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          int k = lane + 32 * q;
+          if (k < S) agg[3 * S + k] = r[q] / d[q];
+        }
+      }
+    } else if (threadIdx.x == 0) {
       T cp = 0, rp = 0;
       for (int k = 0; k < S; ++k) {
         T off = -agg[S + k], dg = 2 * agg[S + k];
@@ -242,7 +401,15 @@ __global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, i
 
 template <typename T>
 void k_mg_coarse_solve(int S, const LevelView<T>& L, int sweeps, T* line_c, T* line_r, T* agg, Stream st) {
-  launch(k_coarse_kernel<T>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+  int kpl = L.tau ? pcr_kpl(S) : 0;
+  if (kpl == 1)
+    launch(k_coarse_kernel<T, 1>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+  else if (kpl == 2)
+    launch(k_coarse_kernel<T, 2>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+  else if (kpl == 4)
+    launch(k_coarse_kernel<T, 4>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+  else
+    launch(k_coarse_kernel<T, 0>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
 }
 
 // ------------------------------------------------------------------ conversions
@@ -269,7 +436,7 @@ void k_mg_store(const T* x, double* dst, i64 n, Stream st) {
 
 #define OT_INST(T)                                                                                              \
   template void k_mg_lap_coef0<T>(const Dims&, const double*, const double*, const double*, T*, Stream);       \
-  template void k_mg_schur_coef0<T>(const Dims&, const double*, const double*, T*, T*, Stream);                \
+  template void k_mg_schur_coef0<T>(const Dims&, const double*, const double*, const double*, T*, T*, Stream); \
   template void k_mg_restrict_coef<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);                  \
   template void k_mg_smooth<T>(int, const LevelView<T>&, int, T*, T*, Stream);                                 \
   template void k_mg_residual<T>(int, const LevelView<T>&, Stream);                                            \

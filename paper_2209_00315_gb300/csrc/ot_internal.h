@@ -58,6 +58,7 @@ enum Id {
 extern bool enabled;        // any group on
 extern unsigned mask;       // bit i: group i on
 extern long long n_launch;  // kernel launches since load (every launch, timing on or off)
+extern int stride;          // time one launch in `stride` of each enabled group
 void begin(int id, Stream s);
 void end(int id, Stream s, double bytes);
 void harvest();
@@ -152,7 +153,8 @@ struct LevelView {
 template <typename T>
 void k_mg_lap_coef0(const Dims& d, const double* rho, const double* r0, const double* r1, T* alpha, Stream st);
 template <typename T>
-void k_mg_schur_coef0(const Dims& d, const double* rho, const double* s, T* alpha, T* tau, Stream st);
+void k_mg_schur_coef0(const Dims& d, const double* phi, const double* rho, const double* s, T* alpha, T* tau,
+                      Stream st);
 template <typename T>
 void k_mg_restrict_coef(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st);
 template <typename T>

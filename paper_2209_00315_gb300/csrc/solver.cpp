@@ -207,7 +207,7 @@ template <typename T>
 static void refresh_t(Workspace& W, Hierarchy<T>& lap, Hierarchy<T>& sch, Stream st) {
   k_mg_lap_coef0<T>(W.d, W.rho, W.r0, W.r1, lap.lv[0].alpha, st);
   for (size_t l = 0; l + 1 < lap.lv.size(); ++l) k_mg_restrict_coef<T>(lap.S, lap.lv[l], lap.lv[l + 1], st);
-  k_mg_schur_coef0<T>(W.d, W.rho, W.s, sch.lv[0].alpha, sch.lv[0].tau, st);
+  k_mg_schur_coef0<T>(W.d, W.phi, W.rho, W.s, sch.lv[0].alpha, sch.lv[0].tau, st);
   for (size_t l = 0; l + 1 < sch.lv.size(); ++l) k_mg_restrict_coef<T>(sch.S, sch.lv[l], sch.lv[l + 1], st);
 }
 

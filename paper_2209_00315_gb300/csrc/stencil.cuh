@@ -413,37 +413,10 @@ OT_HD double adjoint_boundary(const Dims& d, const double* phi, const double* la
 // with x^{-1} = x^K = 0 (Dirichlet in time).  Coefficients are stored
 // [slot][slice][cell].
 
-// Level-0 coefficients of the slice Laplacian A^j: T_e rho~^j_e.
-OT_HD double lap_coef(const Dims& d, const double* rho, const double* r0, const double* r1, int jj, i64 c,
-                      int sl) {
-  Cell q = decode(d.m, c);
-  i64 nb[3];
-  neighbours(d.m, q, nb);
-  if (nb[sl] < 0) return 0.0;
-  double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
-  double ro = rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]));
-  return trans(sl) * 0.5 * (rc + ro);
-}
-
-// Level-0 coefficients of the simplified Schur operator on the coarse grid:
-//   alpha = s^k_C T_E (rho^k_C + rho^k_O)/2  (the Diag(s) A~ part),
-//   tau   = rho^k_C |c'| / dt^2              (the time part of -Diag(rho) B M^{-1} B~).
-OT_HD double schur_coef(const Dims& d, const double* rho, const double* s, int k0, i64 C, int sl) {
-  Cell q = decode(d.n, C);
-  i64 nb[3];
-  neighbours(d.n, q, nb);
-  if (nb[sl] < 0) return 0.0;
-  const double* rk = rho + (i64)k0 * d.Nc;
-  return s[(i64)k0 * d.Nc + C] * trans(sl) * 0.5 * (rk[C] + rk[nb[sl]]);
-}
-
-OT_HD double schur_tau(const Dims& d, const double* rho, int k0, i64 C) {
-  return rho[(i64)k0 * d.Nc + C] * d.area_c / (d.dt * d.dt);
-}
-
 // Coarse coefficient from the fine level (side m -> m/2): the Galerkin sum of
 // the two fine edges making up each coarse edge, halved for the spatial
-// (second-order) part; tau is summed over the four children.
+// (second-order) part; tau is summed over the four children.  The two fine
+// cells below own, in the same slot, the two fine edges of the coarse edge:
 //   coarse L(i,j): slot0 <- L(2i,2j).0, L(2i+1,2j+1).0; slot1 <- L(2i+1,2j).1, L(2i+1,2j+1).1;
 //                  slot2 <- L(2i,2j).2, L(2i+1,2j).2
 //   coarse U(i,j): slot0 <- U(2i,2j).0, U(2i+1,2j+1).0; slot1 <- U(2i,2j).1, U(2i,2j+1).1;
@@ -460,6 +433,60 @@ OT_HD void coarse_coef_sources(int mc, i64 C, int sl, i64 src[2]) {
     else if (sl == 1) { src[0] = encode(m, 1, I, J); src[1] = encode(m, 1, I, J + 1); }
     else { src[0] = encode(m, 1, I, J + 1); src[1] = encode(m, 1, I + 1, J + 1); }
   }
+}
+
+// Level-0 coefficients of the slice Laplacian A^j: T_e rho~^j_e.
+OT_HD double lap_coef(const Dims& d, const double* rho, const double* r0, const double* r1, int jj, i64 c,
+                      int sl) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  neighbours(d.m, q, nb);
+  if (nb[sl] < 0) return 0.0;
+  double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
+  double ro = rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]));
+  return trans(sl) * 0.5 * (rc + ro);
+}
+
+// Level-0 coefficients of the simplified Schur operator on the coarse grid:
+//   alpha = s^k_C T_E (rho^k_C + rho^k_O)/2       (the Diag(s) A~ part)
+//         + rho^k_C T_E (grad phi . n_E)^2         (two-point form of the spatial part
+//                                                   -Diag(rho) B_x M^{-1} B~_x ~ -rho (v.grad)^2),
+//   tau   = rho^k_C |c'| / dt^2                    (the time part of -Diag(rho) B M^{-1} B~).
+// (grad phi . n_E)^2 is the mean over the two fine edges forming the coarse
+// edge and over the potential slices k, k+1 around density time k.
+OT_HD double schur_coef(const Dims& d, const double* phi, const double* rho, const double* s, int k0, i64 C,
+                        int sl) {
+  Cell q = decode(d.n, C);
+  i64 nb[3];
+  neighbours(d.n, q, nb);
+  if (nb[sl] < 0) return 0.0;
+  const double* rk = rho + (i64)k0 * d.Nc;
+  double coef = s[(i64)k0 * d.Nc + C] * trans(sl) * 0.5 * (rk[C] + rk[nb[sl]]);
+  if (phi) {
+    // the slot-sl edges of these two fine children make up the coarse edge
+    i64 src[2];
+    coarse_coef_sources(d.n, C, sl, src);
+    double wf = (sl == 0) ? 0.47140452079103168 / d.m : 1.0 / d.m;  // |w| on the fine grid: sqrt2/3 h or h
+    double g2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      i64 fnb[3];
+      neighbours(d.m, decode(d.m, src[a]), fnb);
+      if (fnb[sl] < 0) continue;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const double* p = phi + (i64)(k0 + j) * d.N;
+        double g = (p[src[a]] - p[fnb[sl]]) / wf;
+        g2 += g * g;
+      }
+    }
+    coef += rk[C] * trans(sl) * 0.25 * g2;
+  }
+  return coef;
+}
+
+OT_HD double schur_tau(const Dims& d, const double* rho, int k0, i64 C) {
+  return rho[(i64)k0 * d.Nc + C] * d.area_c / (d.dt * d.dt);
 }
 
 }  // namespace ot
