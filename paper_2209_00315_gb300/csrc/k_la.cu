@@ -218,131 +218,90 @@ void k_slice_shift(double* x, int S, i64 n, const double* sums, double scale, St
   launch(k_slice_shift_kernel, blocks_for(tot, kThreads, 4096), kThreads, 0, cs(s), x, S, n, sums, scale);
 }
 
-// ------------------------------------------------------------------ multi-dot (CGS)
-template <int NV>
-__global__ void __launch_bounds__(256) k_mdot_kernel(const double* __restrict__ V, i64 ld, int nv,
-                                                     const double* __restrict__ w, i64 n, double* partial) {
-  __shared__ double sm[NV][8];
-  double acc[NV];
+// ------------------------------------------------------------------ Gram-Schmidt passes
+// Dot products: blockIdx.y selects a group of 8 basis vectors, so a thread
+// keeps 8 accumulators (high occupancy); w is re-read per group from L2.
+__global__ void __launch_bounds__(256) k_mdot8_kernel(const double* __restrict__ V, i64 ld, int nv,
+                                                      const double* __restrict__ w, i64 n, double* partial) {
+  __shared__ double sm[8][8];
+  const int v0 = blockIdx.y * 8;
+  const int cnt = min(8, nv - v0);
+  const double* Vg = V + (i64)v0 * ld;
+  double acc[8];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int v = 0; v < 8; ++v) acc[v] = 0.0;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     double wi = w[i];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (v < nv) acc[v] += V[(i64)v * ld + i] * wi;
+    for (int v = 0; v < 8; ++v)
+      if (v < cnt) acc[v] += Vg[(i64)v * ld + i] * wi;
   }
   int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
+  for (int v = 0; v < 8; ++v) {
     double t = warp_sum(acc[v]);
     if (lane == 0) sm[v][wp] = t;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+  if (threadIdx.x < cnt) {
     double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += sm[v][q];
-    partial[(i64)blockIdx.x * (nv + 1) + v] = t;
+    for (int q = 0; q < 8; ++q) t += sm[threadIdx.x][q];
+    partial[(i64)blockIdx.x * (nv + 1) + v0 + threadIdx.x] = t;
   }
 }
 
-template <int NV>
-static void mdot_launch(const double* V, i64 ld, int nv, const double* w, i64 n, double* partial, Stream s) {
-  launch(k_mdot_kernel<NV>, kRedBlocks, 256, 0, cs(s), V, ld, nv, w, n, partial);
+static int mdot_xblocks(int groups) {
+  int bx = kRedBlocks / groups;
+  return bx < 152 ? 152 : bx;
 }
 
 void k_mdot(const double* V, i64 ld, int nv, const double* w, i64 n, double* out, double* partial, Stream s) {
   prof::begin(prof::MDOT, s);
-  int done = 0;
-  while (done < nv) {
-    int c = nv - done;
-    if (c > 32) c = 32;
-    double* pp = partial;
-    if (c <= 8)
-      mdot_launch<8>(V + (i64)done * ld, ld, c, w, n, pp, s);
-    else if (c <= 16)
-      mdot_launch<16>(V + (i64)done * ld, ld, c, w, n, pp, s);
-    else
-      mdot_launch<32>(V + (i64)done * ld, ld, c, w, n, pp, s);
-    launch(k_finish_sum, c, 256, 0, cs(s), pp, kRedBlocks, c + 1, c, out + done);
-    done += c;
-  }
+  int groups = (nv + 7) / 8;
+  int bx = mdot_xblocks(groups);
+  launch(k_mdot8_kernel, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, partial);
+  launch(k_finish_sum, nv, 256, 0, cs(s), partial, bx, nv + 1, nv, out);
   prof::end(prof::MDOT, s, 8.0 * (double)(nv + 1) * (double)n);
 }
 
-// w -= sum_v h[v] V_v, then optional dots with the new w and its squared norm.
-template <int NV>
-__global__ void __launch_bounds__(256) k_mupdate_kernel(const double* __restrict__ V, i64 ld, int nv,
-                                                        const double* __restrict__ h, double* w, i64 n,
-                                                        bool dots, bool norm, double* partial) {
-  __shared__ double sm[NV + 1][8];
-  __shared__ double hs[NV];
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) hs[v] = (v < nv) ? h[v] : 0.0;
+// w -= sum_{v < nv} h[v] V_v (nv <= 64 per launch), streaming; optional squared
+// norm of the new w into partial[block].
+__global__ void __launch_bounds__(256) k_update_kernel(const double* __restrict__ V, i64 ld, int nv,
+                                                       const double* __restrict__ h, double* w, i64 n, bool norm,
+                                                       double* partial) {
+  __shared__ double hs[64];
+  __shared__ double sm[32];
+  for (int v = threadIdx.x; v < 64; v += blockDim.x) hs[v] = (v < nv) ? h[v] : 0.0;
   __syncthreads();
-  double acc[NV + 1];
-#pragma unroll
-  for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+  double acc = 0.0;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double vi[NV];
     double wi = w[i];
+    int v = 0;
+    for (; v + 8 <= nv; v += 8) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      vi[v] = (v < nv) ? V[(i64)v * ld + i] : 0.0;
-      wi -= hs[v] * vi[v];
+      for (int u = 0; u < 8; ++u) wi -= hs[v + u] * V[(i64)(v + u) * ld + i];
     }
+    for (; v < nv; ++v) wi -= hs[v] * V[(i64)v * ld + i];
     w[i] = wi;
-    if (dots) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += vi[v] * wi;
-    }
-    if (norm) acc[NV] += wi * wi;
+    acc += wi * wi;
   }
-  if (!dots && !norm) return;
-  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v <= NV; ++v) {
-    double t = warp_sum(acc[v]);
-    if (lane == 0) sm[v][wp] = t;
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v <= nv; v += blockDim.x) {
-    int src = (v == nv) ? NV : v;
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += sm[src][q];
-    partial[(i64)blockIdx.x * (nv + 1) + v] = t;
-  }
+  if (!norm) return;
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 n, double* out, bool dots,
                bool norm, double* partial, Stream s) {
   prof::begin(prof::MUPDATE, s);
-  struct Closer {
-    Stream s;
-    double b;
-    ~Closer() { prof::end(prof::MUPDATE, s, b); }
-  } closer{s, 8.0 * (double)(nv + 2) * (double)n};
-  if (nv > 32) {
-    // long bases: plain updates in chunks of 32, then separate reductions
-    int done = 0;
-    while (done < nv) {
-      int c = nv - done;
-      if (c > 32) c = 32;
-      launch(k_mupdate_kernel<32>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n, false,
-                                                          false, partial);
-      done += c;
-    }
-    if (dots) k_mdot(V, ld, nv, w, n, out, partial, s);
-    if (norm) k_dot(w, w, n, out + nv, partial, s);
-    return;
+  for (int done = 0; done < nv; done += 64) {
+    int c = nv - done < 64 ? nv - done : 64;
+    bool last = done + c >= nv;
+    launch(k_update_kernel, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n, norm && last,
+           partial);
   }
-  if (nv <= 8)
-    launch(k_mupdate_kernel<8>, kRedBlocks, 256, 0, cs(s), V, ld, nv, h, w, n, dots, norm, partial);
-  else if (nv <= 16)
-    launch(k_mupdate_kernel<16>, kRedBlocks, 256, 0, cs(s), V, ld, nv, h, w, n, dots, norm, partial);
-  else
-    launch(k_mupdate_kernel<32>, kRedBlocks, 256, 0, cs(s), V, ld, nv, h, w, n, dots, norm, partial);
-  if (dots) launch(k_finish_sum, nv, 256, 0, cs(s), partial, kRedBlocks, nv + 1, nv, out);
-  if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial + nv, kRedBlocks, nv + 1, 1, out + nv);
+  if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out + nv);
+  prof::end(prof::MUPDATE, s, 8.0 * (double)(nv + 2) * (double)n);
+  if (dots) k_mdot(V, ld, nv, w, n, out, partial, s);
 }
 
 __global__ void k_mcombine_kernel(const double* __restrict__ Z, i64 ld, int nv, const double* __restrict__ y,

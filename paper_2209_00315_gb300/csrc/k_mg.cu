@@ -31,10 +31,7 @@ static inline int nblk(i64 n) {
 template <typename T>
 __global__ void k_lap_coef0_kernel(Dims d, const double* rho, const double* r0, const double* r1, T* alpha) {
   int S = d.K + 1;
-  i64 tot = (i64)S * d.N;
-  GRID_LOOP(i, tot) {
-    int jj = (int)(i / d.N);
-    i64 c = i - (i64)jj * d.N;
+  SLICE_LOOP(jj, S, c, d.N) {
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) alpha[((i64)sl * S + jj) * d.N + c] = (T)lap_coef(d, rho, r0, r1, jj, c, sl);
   }
@@ -42,17 +39,15 @@ __global__ void k_lap_coef0_kernel(Dims d, const double* rho, const double* r0, 
 
 template <typename T>
 void k_mg_lap_coef0(const Dims& d, const double* rho, const double* r0, const double* r1, T* alpha, Stream st) {
-  launch(k_lap_coef0_kernel<T>, nblk((i64)(d.K + 1) * d.N), kT, 0, cs(st), d, rho, r0, r1, alpha);
+  launch(k_lap_coef0_kernel<T>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, rho, r0, r1, alpha);
 }
 
 template <typename T>
 __global__ void k_schur_coef0_kernel(Dims d, const double* phi, const double* rho, const double* s, T* alpha,
                                      T* tau) {
   int S = d.K;
-  i64 tot = (i64)S * d.Nc;
-  GRID_LOOP(i, tot) {
-    int k0 = (int)(i / d.Nc);
-    i64 C = i - (i64)k0 * d.Nc;
+  SLICE_LOOP(k0, S, C, d.Nc) {
+    i64 i = (i64)k0 * d.Nc + C;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl)
       alpha[((i64)sl * S + k0) * d.Nc + C] = (T)schur_coef(d, phi, rho, s, k0, C, sl);
@@ -63,16 +58,14 @@ __global__ void k_schur_coef0_kernel(Dims d, const double* phi, const double* rh
 template <typename T>
 void k_mg_schur_coef0(const Dims& d, const double* phi, const double* rho, const double* s, T* alpha, T* tau,
                       Stream st) {
-  launch(k_schur_coef0_kernel<T>, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rho, s, alpha, tau);
+  launch(k_schur_coef0_kernel<T>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, alpha, tau);
 }
 
 // ------------------------------------------------------------------ coarse coefficients
 template <typename T>
 __global__ void k_restrict_coef_kernel(int S, LevelView<T> f, LevelView<T> c) {
-  i64 tot = (i64)S * c.nc;
-  GRID_LOOP(i, tot) {
-    int k = (int)(i / c.nc);
-    i64 C = i - (i64)k * c.nc;
+  SLICE_LOOP(k, S, C, c.nc) {
+    i64 i = (i64)k * c.nc + C;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
       i64 src[2];
@@ -91,19 +84,14 @@ __global__ void k_restrict_coef_kernel(int S, LevelView<T> f, LevelView<T> c) {
 
 template <typename T>
 void k_mg_restrict_coef(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st) {
-  launch(k_restrict_coef_kernel<T>, nblk((i64)S * coarse.nc), kT, 0, cs(st), S, fine, coarse);
+  launch(k_restrict_coef_kernel<T>, slice_grid(coarse.nc, S), kT, 0, cs(st), S, fine, coarse);
 }
 
 // ------------------------------------------------------------------ smoothers
 template <typename T>
 __global__ void k_point_smooth_kernel(int S, LevelView<T> L, int color) {
   i64 sq = (i64)L.m * L.m;
-  i64 tot = (i64)S * sq;
-  GRID_LOOP(i, tot) {
-    int k = (int)(i / sq);
-    i64 c = (i64)color * sq + (i - (i64)k * sq);
-    point_gs(S, L, k, c);
-  }
+  SLICE_LOOP(k, S, i, sq) point_gs(S, L, k, (i64)color * sq + i);
 }
 
 template <typename T>
@@ -247,7 +235,7 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
     else
       launch(k_line_smooth_kernel<T>, nblk(sq), kT, 0, cs(st), S, L, color, line_c, line_r);
   } else {
-    launch(k_point_smooth_kernel<T>, nblk((i64)S * sq), kT, 0, cs(st), S, L, color);
+    launch(k_point_smooth_kernel<T>, slice_grid(sq, S), kT, 0, cs(st), S, L, color);
   }
   // per updated cell: b, three coefficients, the neighbours' x, the new x (+ tau for lines)
   prof::end(id, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)sq);
@@ -256,26 +244,23 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
 // ------------------------------------------------------------------ residual and transfers
 template <typename T>
 __global__ void k_residual_kernel(int S, LevelView<T> L) {
-  i64 tot = (i64)S * L.nc;
-  GRID_LOOP(i, tot) {
-    int k = (int)(i / L.nc);
-    L.r[i] = L.b[i] - level_apply(S, L, k, i - (i64)k * L.nc);
+  SLICE_LOOP(k, S, c, L.nc) {
+    i64 i = (i64)k * L.nc + c;
+    L.r[i] = L.b[i] - level_apply(S, L, k, c);
   }
 }
 
 template <typename T>
 void k_mg_residual(int S, const LevelView<T>& L, Stream st) {
   prof::begin(prof::MG_TRANSFER, st);
-  launch(k_residual_kernel<T>, nblk((i64)S * L.nc), kT, 0, cs(st), S, L);
+  launch(k_residual_kernel<T>, slice_grid(L.nc, S), kT, 0, cs(st), S, L);
   prof::end(prof::MG_TRANSFER, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)L.nc);
 }
 
 template <typename T>
 __global__ void k_restrict_kernel(int S, LevelView<T> f, LevelView<T> c) {
-  i64 tot = (i64)S * c.nc;
-  GRID_LOOP(i, tot) {
-    int k = (int)(i / c.nc);
-    i64 C = i - (i64)k * c.nc;
+  SLICE_LOOP(k, S, C, c.nc) {
+    i64 i = (i64)k * c.nc + C;
     i64 ch[4];
     children(c.m, decode(c.m, C), ch);
     const T* rf = f.r + (i64)k * f.nc;
@@ -285,22 +270,17 @@ __global__ void k_restrict_kernel(int S, LevelView<T> f, LevelView<T> c) {
 
 template <typename T>
 void k_mg_restrict(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st) {
-  launch(k_restrict_kernel<T>, nblk((i64)S * coarse.nc), kT, 0, cs(st), S, fine, coarse);
+  launch(k_restrict_kernel<T>, slice_grid(coarse.nc, S), kT, 0, cs(st), S, fine, coarse);
 }
 
 template <typename T>
 __global__ void k_prolong_kernel(int S, LevelView<T> c, LevelView<T> f) {
-  i64 tot = (i64)S * f.nc;
-  GRID_LOOP(i, tot) {
-    int k = (int)(i / f.nc);
-    i64 cf = i - (i64)k * f.nc;
-    f.x[i] += c.x[(i64)k * c.nc + parent_of(f.m, cf)];
-  }
+  SLICE_LOOP(k, S, cf, f.nc) f.x[(i64)k * f.nc + cf] += c.x[(i64)k * c.nc + parent_of(f.m, cf)];
 }
 
 template <typename T>
 void k_mg_prolong(int S, const LevelView<T>& coarse, const LevelView<T>& fine, Stream st) {
-  launch(k_prolong_kernel<T>, nblk((i64)S * fine.nc), kT, 0, cs(st), S, coarse, fine);
+  launch(k_prolong_kernel<T>, slice_grid(fine.nc, S), kT, 0, cs(st), S, coarse, fine);
 }
 
 // ------------------------------------------------------------------ coarsest grid

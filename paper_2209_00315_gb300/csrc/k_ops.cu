@@ -29,19 +29,14 @@ __device__ __forceinline__ double warp_sum2(double v) {
 // ------------------------------------------------------------------ residual
 __global__ void k_residual_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0,
                                       const double* r1, double* F) {
-  i64 tot = (i64)(d.K + 1) * d.N;
-  GRID_LOOP(i, tot) {
-    int jj = (int)(i / d.N);
-    F[i] = residual_phi(d, phi, rho, r0, r1, jj, i - (i64)jj * d.N);
-  }
+  SLICE_LOOP(jj, d.K + 1, c, d.N) F[(i64)jj * d.N + c] = residual_phi(d, phi, rho, r0, r1, jj, c);
 }
 
 __global__ void k_residual_rho_kernel(Dims d, double mu, const double* phi, const double* rho, const double* s,
                                       double* Frho, double* Fs) {
-  i64 tot = (i64)d.K * d.Nc;
-  GRID_LOOP(i, tot) {
-    int k0 = (int)(i / d.Nc);
-    Frho[i] = residual_rho(d, phi, s, k0, i - (i64)k0 * d.Nc);
+  SLICE_LOOP(k0, d.K, C, d.Nc) {
+    i64 i = (i64)k0 * d.Nc + C;
+    Frho[i] = residual_rho(d, phi, s, k0, C);
     Fs[i] = rho[i] * s[i] - mu;
   }
 }
@@ -49,8 +44,8 @@ __global__ void k_residual_rho_kernel(Dims d, double mu, const double* phi, cons
 void k_residual(const Dims& d, double mu, const double* phi, const double* rho, const double* s,
                 const double* r0, const double* r1, double* Fphi, double* Frho, double* Fs, Stream st) {
   prof::begin(prof::RESIDUAL, st);
-  launch(k_residual_phi_kernel, nblk((i64)(d.K + 1) * d.N), kT, 0, cs(st), d, phi, rho, r0, r1, Fphi);
-  launch(k_residual_rho_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, mu, phi, rho, s, Frho, Fs);
+  launch(k_residual_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, Fphi);
+  launch(k_residual_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, mu, phi, rho, s, Frho, Fs);
   prof::end(prof::RESIDUAL, st, 8.0 * (2.0 * (d.K + 1) * d.N + 4.0 * d.K * d.Nc));
 }
 
@@ -73,20 +68,12 @@ __global__ void k_slice_mean_kernel(const double* x, i64 n, double* mean) {
 
 __global__ void k_kkt_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
                                  const double* xp, const double* xr, const double* xmean, bool with_a, double* y) {
-  i64 tot = (i64)(d.K + 1) * d.N;
-  GRID_LOOP(i, tot) {
-    int jj = (int)(i / d.N);
-    y[i] = kkt_phi(d, phi, rho, r0, r1, xp, xr, xmean, with_a, jj, i - (i64)jj * d.N);
-  }
+  SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi(d, phi, rho, r0, r1, xp, xr, xmean, with_a, jj, c);
 }
 
 __global__ void k_kkt_rho_kernel(Dims d, const double* phi, const double* rho, const double* s, const double* xp,
                                  const double* xr, const double* xmean, double* w) {
-  i64 tot = (i64)d.K * d.Nc;
-  GRID_LOOP(i, tot) {
-    int k0 = (int)(i / d.Nc);
-    w[i] = kkt_rho(d, phi, rho, s, xp, xr, xmean, k0, i - (i64)k0 * d.Nc);
-  }
+  SLICE_LOOP(k0, d.K, C, d.Nc) w[(i64)k0 * d.Nc + C] = kkt_rho(d, phi, rho, s, xp, xr, xmean, k0, C);
 }
 
 // y_rho = w - slice mean(w) (P with equal coarse areas); wsum = slice sums of w.
@@ -116,8 +103,8 @@ void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const doub
   const double* xr = x + Np;
   prof::begin(prof::KKT, st);
   launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
-  launch(k_kkt_phi_kernel, nblk(Np), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
-  launch(k_kkt_rho_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
+  launch(k_kkt_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
+  launch(k_kkt_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
   launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, wsum);
   prof::end(prof::KKT, st, 8.0 * (3.0 * Np + 4.0 * d.K * d.Nc));
 }
@@ -126,47 +113,35 @@ void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);
   launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
-  launch(k_kkt_phi_kernel, nblk(Np), kT, 0, cs(st), d, phi, nullptr, nullptr, nullptr, nullptr, yr, yr_mean, false,
+  launch(k_kkt_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, nullptr, nullptr, nullptr, nullptr, yr, yr_mean, false,
                                                  out_phi);
   prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc));
 }
 
 // ------------------------------------------------------------------ Schur operator
 __global__ void k_schur_u_kernel(Dims d, const double* phi, const double* z, double* u) {
-  i64 tot = (i64)(d.K + 1) * d.N;
-  GRID_LOOP(i, tot) {
-    int jj = (int)(i / d.N);
-    u[i] = schur_u(d, phi, z, jj, i - (i64)jj * d.N);
-  }
+  SLICE_LOOP(jj, d.K + 1, c, d.N) u[(i64)jj * d.N + c] = schur_u(d, phi, z, jj, c);
 }
 
 __global__ void k_schur_out_kernel(Dims d, const double* phi, const double* rho, const double* s, const double* u,
                                    const double* z, double* out) {
-  i64 tot = (i64)d.K * d.Nc;
-  GRID_LOOP(i, tot) {
-    int k0 = (int)(i / d.Nc);
-    out[i] = schur_out(d, phi, rho, s, u, z, k0, i - (i64)k0 * d.Nc);
-  }
+  SLICE_LOOP(k0, d.K, C, d.Nc) out[(i64)k0 * d.Nc + C] = schur_out(d, phi, rho, s, u, z, k0, C);
 }
 
 void k_schur_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* z,
                    double* out, double* u, Stream st) {
   prof::begin(prof::SCHUR, st);
-  launch(k_schur_u_kernel, nblk((i64)(d.K + 1) * d.N), kT, 0, cs(st), d, phi, z, u);
-  launch(k_schur_out_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rho, s, u, z, out);
+  launch(k_schur_u_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, z, u);
+  launch(k_schur_out_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, u, z, out);
   prof::end(prof::SCHUR, st, 8.0 * ((double)(d.K + 1) * d.N + 4.0 * d.K * d.Nc));
 }
 
 __global__ void k_atilde_kernel(Dims d, const double* rho, const double* z, double* y) {
-  i64 tot = (i64)d.K * d.Nc;
-  GRID_LOOP(i, tot) {
-    int k0 = (int)(i / d.Nc);
-    y[i] = apply_atilde(d, rho, z, k0, i - (i64)k0 * d.Nc) / d.area_c;
-  }
+  SLICE_LOOP(k0, d.K, C, d.Nc) y[(i64)k0 * d.Nc + C] = apply_atilde(d, rho, z, k0, C) / d.area_c;
 }
 
 void k_atilde_minv(const Dims& d, const double* rho, const double* z, double* y, Stream st) {
-  launch(k_atilde_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, rho, z, y);
+  launch(k_atilde_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, rho, z, y);
 }
 
 // ------------------------------------------------------------------ cost and dual value

@@ -68,17 +68,19 @@ struct Cell {
   int t, I, J;
 };
 
+// In-slice indices stay below 2 m^2 <= 2^25, so 32-bit arithmetic is exact and
+// keeps 64-bit integer division out of every stencil.
 OT_HD Cell decode(int m, i64 c) {
   Cell q;
-  i64 mm = (i64)m * m;
-  q.t = (int)(c / mm);
-  i64 r = c - (i64)q.t * mm;
-  q.J = (int)(r / m);
-  q.I = (int)(r - (i64)q.J * m);
+  int cc = (int)c, mm = m * m;
+  q.t = cc >= mm ? 1 : 0;
+  int r = cc - q.t * mm;
+  q.J = r / m;
+  q.I = r - q.J * m;
   return q;
 }
 
-OT_HD i64 encode(int m, int t, int I, int J) { return (i64)t * m * m + (i64)J * m + I; }
+OT_HD i64 encode(int m, int t, int I, int J) { return (i64)(t * m * m + J * m + I); }
 
 // Neighbour of each edge slot, -1 on the domain boundary (no-flux edges are dropped).
 OT_HD void neighbours(int m, const Cell& q, i64 nb[3]) {
@@ -91,6 +93,22 @@ OT_HD void neighbours(int m, const Cell& q, i64 nb[3]) {
     nb[1] = (q.I > 0) ? encode(m, 0, q.I - 1, q.J) : -1;
     nb[2] = (q.J + 1 < m) ? encode(m, 0, q.I, q.J + 1) : -1;
   }
+}
+
+// The same, also returning the neighbours' (t, I, J) (valid where nb >= 0).
+OT_HD void neighbours(int m, const Cell& q, i64 nb[3], Cell nq[3]) {
+  int to = 1 - q.t;
+  nq[0] = Cell{to, q.I, q.J};
+  if (q.t == 0) {
+    nq[1] = Cell{to, q.I + 1, q.J};
+    nq[2] = Cell{to, q.I, q.J - 1};
+  } else {
+    nq[1] = Cell{to, q.I - 1, q.J};
+    nq[2] = Cell{to, q.I, q.J + 1};
+  }
+  nb[0] = encode(m, nq[0].t, nq[0].I, nq[0].J);
+  nb[1] = (nq[1].I >= 0 && nq[1].I < m) ? encode(m, nq[1].t, nq[1].I, nq[1].J) : -1;
+  nb[2] = (nq[2].J >= 0 && nq[2].J < m) ? encode(m, nq[2].t, nq[2].I, nq[2].J) : -1;
 }
 
 // Coarse triangle (grid side m/2) containing fine cell q (grid side m): the injection J.
@@ -136,7 +154,8 @@ OT_HD double residual_phi(const Dims& d, const double* phi, const double* rho, c
                           const double* r1, int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
   const double* ph = phi + (i64)jj * d.N;
   double ra = rho_at(d, rho, r0, r1, jj, P), rb = rho_at(d, rho, r0, r1, jj + 1, P);
@@ -146,7 +165,7 @@ OT_HD double residual_phi(const Dims& d, const double* phi, const double* rho, c
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
-    double ro = rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]));
+    double ro = rho_bar(d, rho, r0, r1, jj, parent(d.m, nq[sl]));
     acc += trans(sl) * 0.5 * (rc + ro) * (pc - ph[nb[sl]]);
   }
   return acc;
@@ -167,7 +186,8 @@ OT_HD double residual_rho(const Dims& d, const double* phi, const double* s, int
     i64 c = ch[a];
     Cell q = decode(d.m, c);
     i64 nb[3];
-    neighbours(d.m, q, nb);
+    Cell nq[3];
+    neighbours(d.m, q, nb, nq);
     acc += d.area_f * (p1[c] - p0[c]) / d.dt;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
@@ -187,7 +207,8 @@ OT_HD double kkt_phi(const Dims& d, const double* phi, const double* rho, const 
                      const double* xp, const double* xr, const double* xmean, bool with_a, int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
   const double* ph = phi + (i64)jj * d.N;
   const double* xs = xp + (i64)jj * d.N;
@@ -203,7 +224,7 @@ OT_HD double kkt_phi(const Dims& d, const double* phi, const double* rho, const 
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
     i64 o = nb[sl];
-    i64 Po = parent_of(d.m, o);
+    i64 Po = parent(d.m, nq[sl]);
     double ybo = 0.5 * ((ym ? ym[Po] - mm : 0.0) + (yp ? yp[Po] - mp : 0.0));
     double term = 0.5 * (ybc + ybo) * (pc - ph[o]);
     if (with_a) term += 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, Po)) * (xc - xs[o]);
@@ -229,7 +250,8 @@ OT_HD double apply_B(const Dims& d, const double* phi, const double* x, int k0, 
     i64 c = ch[a];
     Cell q = decode(d.m, c);
     i64 nb[3];
-    neighbours(d.m, q, nb);
+    Cell nq[3];
+    neighbours(d.m, q, nb, nq);
     acc += d.area_f * (x1[c] - x0[c]) / d.dt;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
@@ -256,7 +278,8 @@ OT_HD double kkt_rho(const Dims& d, const double* phi, const double* rho, const 
 OT_HD double schur_u(const Dims& d, const double* phi, const double* z, int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
   const double* ph = phi + (i64)jj * d.N;
   const double* zm = (jj >= 1) ? z + (i64)(jj - 1) * d.Nc : nullptr;
@@ -267,7 +290,7 @@ OT_HD double schur_u(const Dims& d, const double* phi, const double* z, int jj, 
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
-    i64 Po = parent_of(d.m, nb[sl]);
+    i64 Po = parent(d.m, nq[sl]);
     double zbo = 0.5 * ((zm ? zm[Po] : 0.0) + (zp ? zp[Po] : 0.0));
     acc += trans(sl) * (ph[c] - ph[nb[sl]]) * (zbc - zbo);
   }
@@ -304,7 +327,8 @@ OT_HD double cost_cell(const Dims& d, const double* phi, const double* rho, cons
                        int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
   const double* ph = phi + (i64)jj * d.N;
   double rc = rho_bar(d, rho, r0, r1, jj, P);
@@ -313,7 +337,7 @@ OT_HD double cost_cell(const Dims& d, const double* phi, const double* rho, cons
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
     double g = ph[c] - ph[nb[sl]];
-    acc += trans(sl) * 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]))) * g * g;
+    acc += trans(sl) * 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent(d.m, nq[sl]))) * g * g;
   }
   return 0.25 * acc;
 }
@@ -324,7 +348,8 @@ OT_HD double cost_cell(const Dims& d, const double* phi, const double* rho, cons
 OT_HD double dual_cell(const Dims& d, const double* phi, const double* r0, const double* r1, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
   const double* pa = phi;
   const double* pb = phi + (i64)d.K * d.N;
@@ -333,7 +358,7 @@ OT_HD double dual_cell(const Dims& d, const double* phi, const double* r0, const
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
-    i64 o = nb[sl], Po = parent_of(d.m, o);
+    i64 o = nb[sl], Po = parent(d.m, nq[sl]);
     double ga = pa[c] - pa[o], gb = pb[c] - pb[o];
     corr += trans(sl) * (0.5 * (r0[P] + r0[Po]) * ga * ga + 0.5 * (r1[P] + r1[Po]) * gb * gb);
   }
@@ -346,14 +371,15 @@ OT_HD double lap_apply(const Dims& d, const double* rho, const double* r0, const
                        i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   const double* xs = x + (i64)jj * d.N;
   double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
   double acc = 0.0;
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
-    acc += trans(sl) * 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]))) * (xs[c] - xs[nb[sl]]);
+    acc += trans(sl) * 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent(d.m, nq[sl]))) * (xs[c] - xs[nb[sl]]);
   }
   return acc;
 }
@@ -440,10 +466,11 @@ OT_HD double lap_coef(const Dims& d, const double* rho, const double* r0, const 
                       int sl) {
   Cell q = decode(d.m, c);
   i64 nb[3];
-  neighbours(d.m, q, nb);
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
   if (nb[sl] < 0) return 0.0;
   double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
-  double ro = rho_bar(d, rho, r0, r1, jj, parent_of(d.m, nb[sl]));
+  double ro = rho_bar(d, rho, r0, r1, jj, parent(d.m, nq[sl]));
   return trans(sl) * 0.5 * (rc + ro);
 }
 
