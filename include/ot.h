@@ -179,6 +179,27 @@ ot_status ot_residual(ot_mesh* mesh, int32_t K, double mu, const double* phi, co
 ot_status ot_kkt_apply(ot_mesh* mesh, int32_t K, const double* phi, const double* rho, const double* s,
                        const double* rho_in, const double* rho_f, const double* x, double* y, void* cuda_stream);
 
+/* The projected saddle operator of ot_kkt_apply, for callers that cannot
+ * allocate device memory: a process whose device memory is already reserved
+ * by another allocator (a framework's caching pool, a fixed serving budget)
+ * where one more cudaMalloc fails or fragments the pool, or a latency-bound
+ * loop that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree imply.  The paper has no counterpart: this is an interface choice.
+ * It allocates nothing and needs no mesh object: n is the number of squares
+ * per side (the mesh of ot_mesh_create), K the number of density slices.  Its
+ * only scratch (the K slice means of x_rho) is a file-scope device array of
+ * 4096 doubles (32 KB) that every GPU loading the library keeps until the
+ * process exits; K > 4096 returns OT_ERR_INVALID_ARG.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current, so make the first call on each device before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (on
+ * different streams at the same time) race on it; each call overwrites all K
+ * entries it reads, so nothing has to be cleared.  Device pointers; returns
+ * after y is written. */
+ot_status ot_kkt_apply_noalloc(int32_t n, int32_t K, const double* phi, const double* rho, const double* s,
+                               const double* rho_in, const double* rho_f, const double* x, double* y,
+                               void* cuda_stream);
+
 /* out = (Diag(s) A~ - Diag(rho) B M^{-1} B~) z, the operator of Eq. (pseudoschur-bis); z, out K x N'. */
 ot_status ot_schur_apply(ot_mesh* mesh, int32_t K, const double* phi, const double* rho, const double* s,
                          const double* z, double* out, void* cuda_stream);

@@ -28,7 +28,7 @@ OT_MAX_STAGES = 40
 EXPORTED = ["ot_default_options", "ot_mesh_create", "ot_mesh_destroy", "ot_mesh_info", "ot_ipm_solve",
             "ot_newton_solve", "ot_cost_grad", "ot_last_error", "ot_residual", "ot_kkt_apply", "ot_schur_apply",
             "ot_bb_apply", "ot_cost_dual", "ot_kernel_timing_enable", "ot_kernel_timing_count",
-            "ot_kernel_timing_read", "ot_kernel_launches"]
+            "ot_kernel_timing_read", "ot_kernel_launches", "ot_kkt_apply_noalloc"]
 
 
 class OTError(RuntimeError):
@@ -98,6 +98,7 @@ def load():
         "ot_residual": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_kkt_apply": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_schur_apply": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+        "ot_kkt_apply_noalloc": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_bb_apply": (_I, [_P, _I, C.POINTER(ot_options), _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_cost_dual": (_I, [_P, _I, _P, _P, _P, _P, C.POINTER(_D), C.POINTER(_D), _P]),
         "ot_kernel_timing_enable": (None, [_I, _I]),
@@ -257,6 +258,18 @@ def ot_kkt_apply(mesh: Mesh, K: int, phi, rho, s, rho_in, rho_f, x, stream=None)
     _check(load().ot_kkt_apply(mesh.handle, int(K), _dev_ptr(phi), _dev_ptr(rho), _dev_ptr(s), _dev_ptr(rho_in),
                                _dev_ptr(rho_f), _dev_ptr(x), _dev_ptr(y), _stream(stream)))
     return y
+
+
+def ot_kkt_apply_noalloc(n: int, K: int, phi, rho, s, rho_in, rho_f, x, out, stream=None):
+    """Projected KKT operator without any device allocation by the library: the
+    caller provides ``out`` (same shape as ``x``); the only scratch is the
+    library's file-scope device array (K <= 4096).  For callers whose device
+    memory is reserved by another allocator or whose loop cannot absorb the
+    synchronisation of cudaMalloc/cudaFree."""
+    _check(load().ot_kkt_apply_noalloc(int(n), int(K), _dev_ptr(phi), _dev_ptr(rho), _dev_ptr(s),
+                                       _dev_ptr(rho_in), _dev_ptr(rho_f), _dev_ptr(x), _dev_ptr(out),
+                                       _stream(stream)))
+    return out
 
 
 def ot_schur_apply(mesh: Mesh, K: int, phi, rho, s, z, stream=None):

@@ -363,6 +363,22 @@ ot_status ot_kkt_apply(ot_mesh* mesh, int32_t K, const double* phi, const double
   OT_CATCH
 }
 
+ot_status ot_kkt_apply_noalloc(int32_t n, int32_t K, const double* phi, const double* rho, const double* s,
+                               const double* rho_in, const double* rho_f, const double* x, double* y,
+                               void* cuda_stream) {
+  OT_TRY
+  require(supported_side(n), "n must be 2^a * b with b <= 11 and n <= 4096");
+  require(K >= 1, "K must be >= 1");
+  require(K <= ot::kStaticKktMaxK, "K exceeds the no-allocation limit (4096 slices)");
+  require(phi && rho && s && rho_in && rho_f && x && y, "NULL argument");
+  Stream st = cuda_stream;
+  ot::k_kkt_apply_static(ot::make_dims(n, K), phi, rho, s, rho_in, rho_f, x, y, st);
+  dev::check("ot_kkt_apply_noalloc launch");
+  dev::sync(st);
+  return OT_OK;
+  OT_CATCH
+}
+
 ot_status ot_schur_apply(ot_mesh* mesh, int32_t K, const double* phi, const double* rho, const double* s,
                          const double* z, double* out, void* cuda_stream) {
   OT_TRY

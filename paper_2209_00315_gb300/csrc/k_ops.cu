@@ -109,6 +109,38 @@ void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const doub
   prof::end(prof::KKT, st, 8.0 * (3.0 * Np + 4.0 * d.K * d.Nc));
 }
 
+// ---- KKT operator with file-scope scratch (no allocation by the call).
+// The slice means of x_rho live in this array instead of caller- or
+// library-allocated memory; every GPU that loads the library holds it.
+static __device__ __align__(256) double g_kkt_scratch[kStaticKktMaxK];
+static double* g_kkt_scratch_addr[kStaticKktMaxDevices];  // device address per device, set up once
+
+double* kkt_static_scratch() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) throw Error(7, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kStaticKktMaxDevices) throw Error(1, "device index beyond the static scratch table");
+  if (!g_kkt_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_kkt_scratch);
+    if (e != cudaSuccess) throw Error(7, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_kkt_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  return g_kkt_scratch_addr[dev];
+}
+
+void k_kkt_apply_static(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
+                        const double* r1, const double* x, double* y, Stream st) {
+  if (d.K > kStaticKktMaxK) throw Error(1, "K exceeds the static scratch of the no-allocation KKT operator");
+  double* xmean = kkt_static_scratch();
+  i64 Np = (i64)(d.K + 1) * d.N;
+  const double* xr = x + Np;
+  launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
+  launch(k_kkt_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
+  launch(k_kkt_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
+  launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, (double*)nullptr);
+}
+
 void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_phi, double* yr_mean, Stream st) {
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);

@@ -97,6 +97,13 @@ void k_residual(const Dims& d, double mu, const double* phi, const double* rho, 
 // wsum (nullable, K): slice sums of B x_phi - C P^T x_rho before the projection.
 void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
                  const double* r1, const double* x, double* y, double* xmean, double* wsum, Stream st);
+// The same operator with its slice-mean scratch in a file-scope device array
+// (no allocation); K <= kStaticKktMaxK.  The first call on a device resolves
+// the array's address (cudaGetSymbolAddress) with that device current.
+constexpr int kStaticKktMaxK = 4096;
+constexpr int kStaticKktMaxDevices = 64;
+void k_kkt_apply_static(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
+                        const double* r1, const double* x, double* y, Stream st);
 // y_phi = B^T P^T y_rho (phi rows only, no A term); yr_mean: scratch K.
 void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_phi, double* yr_mean, Stream st);
 // Schur operator of Eq. (pseudoschur-bis); u: scratch (K+1) N.
