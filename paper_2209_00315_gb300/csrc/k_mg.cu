@@ -14,6 +14,8 @@
 // stencil.cuh.
 #include <cuda_runtime.h>
 
+#include <unordered_map>
+
 #include "launch.cuh"
 #include "mg_body.cuh"
 
@@ -290,7 +292,7 @@ void k_mg_prolong(int S, const LevelView<T>& coarse, const LevelView<T>& fine, S
 // tau_G = sum of tau over the cells), followed by `sweeps` more sweeps.
 // KPL > 0: time lines and the aggregate system by warp PCR; KPL = 0: Thomas per thread.
 template <typename T, int KPL>
-__global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, int sweeps, T* lc, T* lr, T* agg) {
+__device__ void coarse_body(int S, const LevelView<T>& L, int sweeps, T* lc, T* lr, T* agg) {
   i64 sq = (i64)L.m * L.m;
   i64 tot = (i64)S * L.nc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -379,6 +381,11 @@ __global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, i
   }
 }
 
+template <typename T, int KPL>
+__global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, int sweeps, T* lc, T* lr, T* agg) {
+  coarse_body<T, KPL>(S, L, sweeps, lc, lr, agg);
+}
+
 template <typename T>
 void k_mg_coarse_solve(int S, const LevelView<T>& L, int sweeps, T* line_c, T* line_r, T* agg, Stream st) {
   int kpl = L.tau ? pcr_kpl(S) : 0;
@@ -390,6 +397,223 @@ void k_mg_coarse_solve(int S, const LevelView<T>& L, int sweeps, T* line_c, T* l
     launch(k_coarse_kernel<T, 4>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
   else
     launch(k_coarse_kernel<T, 0>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+}
+
+// ------------------------------------------------------------------ fused lower levels
+// The small levels of a V-cycle (from levels[0] down to the coarsest) in one
+// launch, staged in shared memory: the CTA copies every fused level's
+// coefficients and the first level's right-hand side in, runs the same
+// operations in the same order as the per-level kernels with block barriers
+// between phases, and writes the first level's x back.
+template <typename T>
+struct LevelSet {
+  int n;
+  LevelView<T> L[16];
+};
+
+// Carve shared-memory views of the fused levels (S_view slices each) and copy
+// coefficients (slice `slice0` onwards) and the first level's b into them.
+template <typename T>
+__device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int S, int S_view, int slice0) {
+  if (threadIdx.x == 0) {
+    T* p = smem;
+    s.n = g.n;
+    for (int l = 0; l < g.n; ++l) {
+      const LevelView<T>& G = g.L[l];
+      LevelView<T>& V = s.L[l];
+      const i64 n1 = (i64)S_view * G.nc;
+      V.m = G.m;
+      V.nc = G.nc;
+      V.alpha = p;
+      p += 3 * n1;
+      V.tau = G.tau ? p : nullptr;
+      if (G.tau) p += n1;
+      V.x = p;
+      p += n1;
+      V.b = p;
+      p += n1;
+      V.r = p;
+      p += n1;
+    }
+  }
+  __syncthreads();
+  for (int l = 0; l < g.n; ++l) {
+    const LevelView<T>& G = g.L[l];
+    const LevelView<T>& V = s.L[l];
+    const i64 n1 = (i64)S_view * G.nc;
+    for (i64 i = threadIdx.x; i < 3 * n1; i += blockDim.x) {
+      int sl = (int)(i / n1);
+      i64 rem = i - (i64)sl * n1;
+      int kv = (int)(rem / G.nc);
+      i64 c = rem - (i64)kv * G.nc;
+      V.alpha[i] = G.alpha[((i64)sl * S + slice0 + kv) * G.nc + c];
+    }
+    if (G.tau)
+      for (i64 i = threadIdx.x; i < n1; i += blockDim.x) V.tau[i] = G.tau[(i64)slice0 * G.nc + i];
+    if (l == 0)
+      for (i64 i = threadIdx.x; i < n1; i += blockDim.x) V.b[i] = G.b[(i64)slice0 * G.nc + i];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+size_t fused_smem_bytes(const LevelView<T>* lv, int nlev, int S_view, bool tc) {
+  size_t cells = 0;
+  for (int l = 0; l < nlev; ++l) cells += (size_t)S_view * lv[l].nc;
+  return sizeof(T) * cells * (tc ? 7 : 6) + (tc ? sizeof(T) * 4 * (size_t)S_view : 0);
+}
+
+// Slice Laplacians: one CTA per slice (blockIdx.x), point red-black GS, the
+// slice's levels in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lap_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = blockIdx.x;
+  __shared__ LevelSet<T> ls;
+  stage_levels(gls, ls, reinterpret_cast<T*>(smem_raw), S, 1, k);
+  const int last = ls.n - 1;
+  for (int l = 0; l <= last; ++l) {
+    const LevelView<T>& L = ls.L[l];
+    const i64 sq = (i64)L.m * L.m;
+    for (i64 i = threadIdx.x; i < L.nc; i += blockDim.x) L.x[i] = 0;
+    __syncthreads();
+    const int sweeps = (l == last) ? nuc : nu;
+    for (int it = 0; it < sweeps; ++it)
+      for (int col = 0; col < 2; ++col) {
+        for (i64 i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)col * sq + i);
+        __syncthreads();
+      }
+    if (l == last) break;
+    for (i64 c = threadIdx.x; c < L.nc; c += blockDim.x) L.r[c] = L.b[c] - level_apply(1, L, 0, c);
+    __syncthreads();
+    const LevelView<T>& Lc = ls.L[l + 1];
+    for (i64 C = threadIdx.x; C < Lc.nc; C += blockDim.x) {
+      i64 ch[4];
+      children(Lc.m, decode(Lc.m, C), ch);
+      Lc.b[C] = L.r[ch[0]] + L.r[ch[1]] + L.r[ch[2]] + L.r[ch[3]];
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= 0; --l) {
+    const LevelView<T>& L = ls.L[l];
+    const LevelView<T>& Lc = ls.L[l + 1];
+    const i64 sq = (i64)L.m * L.m;
+    for (i64 c = threadIdx.x; c < L.nc; c += blockDim.x) L.x[c] += Lc.x[parent_of(L.m, c)];
+    __syncthreads();
+    for (int it = 0; it < nu; ++it)
+      for (int col = 1; col >= 0; --col) {
+        for (i64 i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)col * sq + i);
+        __syncthreads();
+      }
+  }
+  const LevelView<T>& G0 = gls.L[0];
+  for (i64 i = threadIdx.x; i < G0.nc; i += blockDim.x) G0.x[(i64)k * G0.nc + i] = ls.L[0].x[i];
+}
+
+// Space-time Schur operator: one CTA for all slices, time lines by warp PCR,
+// all fused levels in shared memory; the coarsest level adds the aggregate
+// correction of k_coarse_kernel.
+template <typename T, int KPL>
+__global__ void __launch_bounds__(1024) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ LevelSet<T> ls;
+  stage_levels(gls, ls, reinterpret_cast<T*>(smem_raw), S, S, 0);
+  T* agg = ls.L[ls.n - 1].r + (i64)S * ls.L[ls.n - 1].nc;
+  const int last = ls.n - 1;
+  for (int l = 0; l < last; ++l) {
+    const LevelView<T>& L = ls.L[l];
+    const i64 sq = (i64)L.m * L.m, tot = (i64)S * L.nc;
+    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] = 0;
+    __syncthreads();
+    for (int it = 0; it < nu; ++it)
+      for (int col = 0; col < 2; ++col) {
+        for (i64 w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
+        __syncthreads();
+      }
+    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) {
+      int k = (int)(i / L.nc);
+      L.r[i] = L.b[i] - level_apply(S, L, k, i - (i64)k * L.nc);
+    }
+    __syncthreads();
+    const LevelView<T>& Lc = ls.L[l + 1];
+    for (i64 i = threadIdx.x; i < (i64)S * Lc.nc; i += blockDim.x) {
+      int k = (int)(i / Lc.nc);
+      i64 C = i - (i64)k * Lc.nc;
+      i64 ch[4];
+      children(Lc.m, decode(Lc.m, C), ch);
+      const T* rf = L.r + (i64)k * L.nc;
+      Lc.b[i] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
+    }
+    __syncthreads();
+  }
+  coarse_body<T, KPL>(S, ls.L[last], nuc, (T*)nullptr, (T*)nullptr, agg);
+  __syncthreads();
+  for (int l = last - 1; l >= 0; --l) {
+    const LevelView<T>& L = ls.L[l];
+    const LevelView<T>& Lc = ls.L[l + 1];
+    const i64 sq = (i64)L.m * L.m, tot = (i64)S * L.nc;
+    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) {
+      int k = (int)(i / L.nc);
+      L.x[i] += Lc.x[(i64)k * Lc.nc + parent_of(L.m, i - (i64)k * L.nc)];
+    }
+    __syncthreads();
+    for (int it = 0; it < nu; ++it)
+      for (int col = 1; col >= 0; --col) {
+        for (i64 w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
+        __syncthreads();
+      }
+  }
+  const LevelView<T>& G0 = gls.L[0];
+  for (i64 i = threadIdx.x; i < (i64)S * G0.nc; i += blockDim.x) G0.x[i] = ls.L[0].x[i];
+}
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per size).
+template <typename Kern>
+static void set_smem(Kern k, size_t bytes) {
+  static std::unordered_map<const void*, size_t> granted;
+  if (bytes <= 48 * 1024) return;
+  size_t& g = granted[reinterpret_cast<const void*>(k)];
+  if (bytes <= g) return;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) throw Error(7, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  g = bytes;
+}
+
+template <typename T>
+size_t k_mg_fused_smem(int S, const LevelView<T>* levels, int nlev) {
+  bool tc = levels[0].tau != nullptr;
+  return fused_smem_bytes(levels, nlev, tc ? S : 1, tc);
+}
+
+template <typename T>
+void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int nuc, T* line_c, T* line_r, T* agg,
+                      Stream st) {
+  (void)line_c, (void)line_r, (void)agg;
+  if (nlev < 1 || nlev > 16) throw Error(1, "fused multigrid levels out of range");
+  LevelSet<T> ls;
+  ls.n = nlev;
+  for (int i = 0; i < nlev; ++i) ls.L[i] = levels[i];
+  const size_t bytes = k_mg_fused_smem(S, levels, nlev);
+  if (bytes > kFusedSmemLimit) throw Error(1, "fused multigrid levels exceed shared memory");
+  if (!levels[0].tau) {
+    set_smem(k_lap_lower_kernel<T>, bytes);
+    launch(k_lap_lower_kernel<T>, S, 256, bytes, cs(st), S, ls, nu, nuc);
+    return;
+  }
+  int kpl = pcr_kpl(S);
+  if (kpl == 1) {
+    set_smem(k_sch_lower_kernel<T, 1>, bytes);
+    launch(k_sch_lower_kernel<T, 1>, 1, 1024, bytes, cs(st), S, ls, nu, nuc);
+  } else if (kpl == 2) {
+    set_smem(k_sch_lower_kernel<T, 2>, bytes);
+    launch(k_sch_lower_kernel<T, 2>, 1, 1024, bytes, cs(st), S, ls, nu, nuc);
+  } else if (kpl == 4) {
+    set_smem(k_sch_lower_kernel<T, 4>, bytes);
+    launch(k_sch_lower_kernel<T, 4>, 1, 1024, bytes, cs(st), S, ls, nu, nuc);
+  } else {
+    throw Error(1, "fused Schur levels need K <= 128");
+  }
 }
 
 // ------------------------------------------------------------------ conversions
@@ -423,6 +647,8 @@ void k_mg_store(const T* x, double* dst, i64 n, Stream st) {
   template void k_mg_restrict<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);                       \
   template void k_mg_prolong<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);                        \
   template void k_mg_coarse_solve<T>(int, const LevelView<T>&, int, T*, T*, T*, Stream);                       \
+  template void k_mg_lower_cycle<T>(int, const LevelView<T>*, int, int, int, T*, T*, T*, Stream);              \
+  template size_t k_mg_fused_smem<T>(int, const LevelView<T>*, int);                                           \
   template void k_mg_load<T>(const double*, double, T*, T*, i64, Stream);                                      \
   template void k_mg_store<T>(const T*, double*, i64, Stream);
 OT_INST(float)

@@ -174,6 +174,16 @@ template <typename T>
 void k_mg_prolong(int S, const LevelView<T>& coarse, const LevelView<T>& fine, Stream st);
 template <typename T>
 void k_mg_coarse_solve(int S, const LevelView<T>& L, int sweeps, T* line_c, T* line_r, T* agg, Stream st);
+// The V-cycle from levels[0] to levels[nlev-1] (the coarsest) in one launch: x
+// of every level zeroed, nu pre/post sweeps, nuc sweeps (and, for the
+// space-time hierarchy, the aggregate correction) on the coarsest level.
+template <typename T>
+void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int nuc, T* line_c, T* line_r, T* agg,
+                      Stream st);
+// Shared memory the fused cycle over these levels needs; it must stay <= kFusedSmemLimit.
+template <typename T>
+size_t k_mg_fused_smem(int S, const LevelView<T>* levels, int nlev);
+constexpr size_t kFusedSmemLimit = 200 * 1024;
 // b = (T)(scale * src); x = 0
 template <typename T>
 void k_mg_load(const double* src, double scale, T* b, T* x, i64 n, Stream st);

@@ -41,6 +41,18 @@ void Hierarchy<T>::build(int m0, int S_, bool tc) {
   agg = (T*)dev::alloc(sizeof(T) * 4 * (size_t)S);
   acc = (T*)dev::alloc(v0);
   bsave = (T*)dev::alloc(v0);
+  // small levels run fused in one launch from shared memory: per-slice CTAs up
+  // to side 32 for the slice Laplacians, one CTA up to side 8 for the
+  // space-time operator (K <= 128); the largest such tail that fits.
+  const int fuse_side = tc ? 8 : 32;
+  fuse_from = lv.size();
+  if (!tc || S <= 128)
+    for (size_t l = 0; l < lv.size(); ++l)
+      if (lv[l].m <= fuse_side &&
+          k_mg_fused_smem<T>(S, lv.data() + l, (int)(lv.size() - l)) <= kFusedSmemLimit) {
+        fuse_from = l;
+        break;
+      }
 }
 
 template <typename T>
@@ -158,6 +170,10 @@ Workspace::~Workspace() {
 template <typename T>
 static void vcycle(Hierarchy<T>& H, size_t l, int nu, int nuc, Stream st) {
   LevelView<T>& L = H.lv[l];
+  if (l == H.fuse_from) {
+    k_mg_lower_cycle<T>(H.S, H.lv.data() + l, (int)(H.lv.size() - l), nu, nuc, H.line_c, H.line_r, H.agg, st);
+    return;
+  }
   if (l + 1 == H.lv.size()) {
     k_mg_coarse_solve<T>(H.S, L, nuc, H.line_c, H.line_r, H.agg, st);
     return;

@@ -18,6 +18,7 @@ struct Hierarchy {
   T* agg = nullptr;        // 4 S
   T* acc = nullptr;        // level-0 accumulator for repeated cycles
   T* bsave = nullptr;      // level-0 right-hand side for repeated cycles
+  size_t fuse_from = 0;    // first level handled by the fused lower-cycle kernel (lv.size(): none)
   void build(int m0, int S, bool time_coupled);
   void release();
   bool built() const { return !lv.empty(); }
