@@ -194,44 +194,47 @@ __global__ void k_finish_sum(const double* partial, int nblocks, int stride, int
 }
 
 // ------------------------------------------------------------------ slice sums
-__global__ void k_slice_sums_kernel(const double* x, i64 n, double scale, double* sums) {
+template <typename T>
+__global__ void k_slice_sums_kernel(const T* x, i64 n, double scale, T* sums) {
   __shared__ double sm[32];
-  const double* xs = x + (i64)blockIdx.x * n;
+  const T* xs = x + (i64)blockIdx.x * n;
   double a = 0.0;
-  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += xs[i];
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += (double)xs[i];
   a = block_sum(a, sm);
-  if (threadIdx.x == 0) sums[blockIdx.x] = scale * a;
+  if (threadIdx.x == 0) sums[blockIdx.x] = (T)(scale * a);
 }
 
 void k_slice_sums(const double* x, int S, i64 n, double scale, double* sums, Stream s) {
-  launch(k_slice_sums_kernel, S, 512, 0, cs(s), x, n, scale, sums);
+  launch(k_slice_sums_kernel<double>, S, 512, 0, cs(s), x, n, scale, sums);
 }
 
-__global__ void k_slice_shift_kernel(double* x, int S, i64 n, const double* sums, double scale) {
+template <typename T>
+__global__ void k_slice_shift_kernel(T* x, int S, i64 n, const T* sums, double scale) {
   i64 tot = (i64)S * n;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < tot; i += (i64)gridDim.x * blockDim.x)
-    x[i] -= scale * sums[i / n];
+    x[i] -= (T)(scale * (double)sums[i / n]);
 }
 
 void k_slice_shift(double* x, int S, i64 n, const double* sums, double scale, Stream s) {
   i64 tot = (i64)S * n;
-  launch(k_slice_shift_kernel, blocks_for(tot, kThreads, 4096), kThreads, 0, cs(s), x, S, n, sums, scale);
+  launch(k_slice_shift_kernel<double>, blocks_for(tot, kThreads, 4096), kThreads, 0, cs(s), x, S, n, sums, scale);
 }
 
 // ------------------------------------------------------------------ Gram-Schmidt passes
 // Dot products: blockIdx.y selects a group of 8 basis vectors, so a thread
 // keeps 8 accumulators (high occupancy); w is re-read per group from L2.
-__global__ void __launch_bounds__(256) k_mdot8_kernel(const double* __restrict__ V, i64 ld, int nv,
-                                                      const double* __restrict__ w, i64 n, double* partial) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_mdot8_kernel(const T* __restrict__ V, i64 ld, int nv,
+                                                      const T* __restrict__ w, i64 n, double* partial) {
   __shared__ double sm[8][8];
   const int v0 = blockIdx.y * 8;
   const int cnt = min(8, nv - v0);
-  const double* Vg = V + (i64)v0 * ld;
-  double acc[8];
+  const T* Vg = V + (i64)v0 * ld;
+  T acc[8];
 #pragma unroll
-  for (int v = 0; v < 8; ++v) acc[v] = 0.0;
+  for (int v = 0; v < 8; ++v) acc[v] = 0;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double wi = w[i];
+    T wi = w[i];
 #pragma unroll
     for (int v = 0; v < 8; ++v)
       if (v < cnt) acc[v] += Vg[(i64)v * ld + i] * wi;
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(256) k_mdot8_kernel(const double* __restrict__
   int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
   for (int v = 0; v < 8; ++v) {
-    double t = warp_sum(acc[v]);
+    double t = warp_sum((double)acc[v]);
     if (lane == 0) sm[v][wp] = t;
   }
   __syncthreads();
@@ -259,23 +262,24 @@ void k_mdot(const double* V, i64 ld, int nv, const double* w, i64 n, double* out
   prof::begin(prof::MDOT, s);
   int groups = (nv + 7) / 8;
   int bx = mdot_xblocks(groups);
-  launch(k_mdot8_kernel, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, partial);
+  launch(k_mdot8_kernel<double>, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, partial);
   launch(k_finish_sum, nv, 256, 0, cs(s), partial, bx, nv + 1, nv, out);
   prof::end(prof::MDOT, s, 8.0 * (double)(nv + 1) * (double)n);
 }
 
 // w -= sum_{v < nv} h[v] V_v (nv <= 64 per launch), streaming; optional squared
 // norm of the new w into partial[block].
-__global__ void __launch_bounds__(256) k_update_kernel(const double* __restrict__ V, i64 ld, int nv,
-                                                       const double* __restrict__ h, double* w, i64 n, bool norm,
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_kernel(const T* __restrict__ V, i64 ld, int nv,
+                                                       const double* __restrict__ h, T* w, i64 n, bool norm,
                                                        double* partial) {
-  __shared__ double hs[64];
+  __shared__ T hs[64];
   __shared__ double sm[32];
-  for (int v = threadIdx.x; v < 64; v += blockDim.x) hs[v] = (v < nv) ? h[v] : 0.0;
+  for (int v = threadIdx.x; v < 64; v += blockDim.x) hs[v] = (v < nv) ? (T)h[v] : (T)0;
   __syncthreads();
-  double acc = 0.0;
+  T acc = 0;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double wi = w[i];
+    T wi = w[i];
     int v = 0;
     for (; v + 8 <= nv; v += 8) {
 #pragma unroll
@@ -286,8 +290,8 @@ __global__ void __launch_bounds__(256) k_update_kernel(const double* __restrict_
     acc += wi * wi;
   }
   if (!norm) return;
-  acc = block_sum(acc, sm);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  double a = block_sum((double)acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
 }
 
 void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 n, double* out, bool dots,
@@ -296,7 +300,7 @@ void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 
   for (int done = 0; done < nv; done += 64) {
     int c = nv - done < 64 ? nv - done : 64;
     bool last = done + c >= nv;
-    launch(k_update_kernel, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n, norm && last,
+    launch(k_update_kernel<double>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n, norm && last,
            partial);
   }
   if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out + nv);
@@ -304,13 +308,14 @@ void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 
   if (dots) k_mdot(V, ld, nv, w, n, out, partial, s);
 }
 
-__global__ void k_mcombine_kernel(const double* __restrict__ Z, i64 ld, int nv, const double* __restrict__ y,
-                                  double* x, i64 n) {
-  __shared__ double ys[64];
-  for (int v = threadIdx.x; v < nv && v < 64; v += blockDim.x) ys[v] = y[v];
+template <typename T>
+__global__ void k_mcombine_kernel(const T* __restrict__ Z, i64 ld, int nv, const double* __restrict__ y, T* x,
+                                  i64 n) {
+  __shared__ T ys[64];
+  for (int v = threadIdx.x; v < nv && v < 64; v += blockDim.x) ys[v] = (T)y[v];
   __syncthreads();
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double a = x[i];
+    T a = x[i];
     for (int v = 0; v < nv; ++v) a += ys[v] * Z[(i64)v * ld + i];
     x[i] = a;
   }
@@ -322,24 +327,25 @@ void k_mcombine(const double* Z, i64 ld, int nv, const double* y, double* x, i64
   while (done < nv) {
     int c = nv - done;
     if (c > 64) c = 64;
-    launch(k_mcombine_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), Z + (i64)done * ld, ld, c,
+    launch(k_mcombine_kernel<double>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), Z + (i64)done * ld, ld, c,
                                                                              y + done, x, n);
     done += c;
   }
   prof::end(prof::MCOMBINE, s, 8.0 * (double)(nv + 2) * (double)n);
 }
 
-__global__ void k_dot_kernel(const double* x, const double* y, i64 n, double* partial) {
+template <typename T>
+__global__ void k_dot_kernel(const T* x, const T* y, i64 n, double* partial) {
   __shared__ double sm[32];
-  double a = 0.0;
+  T t = 0;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-    a += x[i] * y[i];
-  a = block_sum(a, sm);
+    t += x[i] * y[i];
+  double a = block_sum((double)t, sm);
   if (threadIdx.x == 0) partial[blockIdx.x] = a;
 }
 
 void k_dot(const double* x, const double* y, i64 n, double* out, double* partial, Stream s) {
-  launch(k_dot_kernel, kRedBlocks, kThreads, 0, cs(s), x, y, n, partial);
+  launch(k_dot_kernel<double>, kRedBlocks, kThreads, 0, cs(s), x, y, n, partial);
   launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out);
 }
 
@@ -351,21 +357,23 @@ void k_axpby(double a, const double* x, double b, double* y, i64 n, Stream s) {
   launch(k_axpby_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), a, x, b, y, n);
 }
 
-__global__ void k_scale_inv_norm_kernel(const double* x, const double* nrm2, double* y, i64 n) {
-  double f = 1.0 / sqrt(nrm2[0]);
+template <typename T>
+__global__ void k_scale_inv_norm_kernel(const T* x, const double* nrm2, T* y, i64 n) {
+  T f = (T)(1.0 / sqrt(nrm2[0]));
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = x[i] * f;
 }
 void k_scale_by_inv_norm(const double* x, const double* nrm2, double* y, i64 n, Stream s) {
-  launch(k_scale_inv_norm_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, nrm2, y, n);
+  launch(k_scale_inv_norm_kernel<double>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, nrm2, y, n);
 }
 
-__global__ void k_scale_kernel(const double* x, double a, double* y, i64 n) {
+template <typename T>
+__global__ void k_scale_kernel(const T* x, T a, T* y, i64 n) {
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = a * x[i];
 }
 void k_scale(const double* x, double a, double* y, i64 n, Stream s) {
-  launch(k_scale_kernel, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, a, y, n);
+  launch(k_scale_kernel<double>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, a, y, n);
 }
 __global__ void k_fill_kernel(double* x, double v, i64 n) {
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) x[i] = v;
@@ -434,4 +442,55 @@ void k_min(const double* x, i64 n, double* out, double* partial, Stream s) {
   launch(k_min_finish, 1, 32, 0, cs(s), partial, kRedBlocks, out);
 }
 
+}  // namespace ot
+
+namespace ot {
+// ---- FP32 vectors (the preconditioner's inner Krylov solve in mixed precision)
+void k_slice_sums(const float* x, int S, i64 n, double scale, float* sums, Stream s) {
+  launch(k_slice_sums_kernel<float>, S, 512, 0, cs(s), x, n, scale, sums);
+}
+void k_slice_shift(float* x, int S, i64 n, const float* sums, double scale, Stream s) {
+  i64 tot = (i64)S * n;
+  launch(k_slice_shift_kernel<float>, blocks_for(tot, kThreads, 4096), kThreads, 0, cs(s), x, S, n, sums, scale);
+}
+void k_mdot(const float* V, i64 ld, int nv, const float* w, i64 n, double* out, double* partial, Stream s) {
+  prof::begin(prof::MDOT, s);
+  int groups = (nv + 7) / 8;
+  int bx = mdot_xblocks(groups);
+  launch(k_mdot8_kernel<float>, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, partial);
+  launch(k_finish_sum, nv, 256, 0, cs(s), partial, bx, nv + 1, nv, out);
+  prof::end(prof::MDOT, s, 4.0 * (double)(nv + 1) * (double)n);
+}
+void k_mupdate(const float* V, i64 ld, int nv, const double* h, float* w, i64 n, double* out, bool dots, bool norm,
+               double* partial, Stream s) {
+  prof::begin(prof::MUPDATE, s);
+  for (int done = 0; done < nv; done += 64) {
+    int c = nv - done < 64 ? nv - done : 64;
+    bool last = done + c >= nv;
+    launch(k_update_kernel<float>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n,
+           norm && last, partial);
+  }
+  if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out + nv);
+  prof::end(prof::MUPDATE, s, 4.0 * (double)(nv + 2) * (double)n);
+  if (dots) k_mdot(V, ld, nv, w, n, out, partial, s);
+}
+void k_mcombine(const float* Z, i64 ld, int nv, const double* y, float* x, i64 n, Stream s) {
+  prof::begin(prof::MCOMBINE, s);
+  for (int done = 0; done < nv; done += 64) {
+    int c = nv - done < 64 ? nv - done : 64;
+    launch(k_mcombine_kernel<float>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), Z + (i64)done * ld, ld, c,
+           y + done, x, n);
+  }
+  prof::end(prof::MCOMBINE, s, 4.0 * (double)(nv + 2) * (double)n);
+}
+void k_dot(const float* x, const float* y, i64 n, double* out, double* partial, Stream s) {
+  launch(k_dot_kernel<float>, kRedBlocks, kThreads, 0, cs(s), x, y, n, partial);
+  launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out);
+}
+void k_scale_by_inv_norm(const float* x, const double* nrm2, float* y, i64 n, Stream s) {
+  launch(k_scale_inv_norm_kernel<float>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, nrm2, y, n);
+}
+void k_scale(const float* x, double a, float* y, i64 n, Stream s) {
+  launch(k_scale_kernel<float>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, (float)a, y, n);
+}
 }  // namespace ot

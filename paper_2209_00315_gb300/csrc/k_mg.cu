@@ -220,6 +220,73 @@ __global__ void __launch_bounds__(256) k_line_pcr_kernel(int S, LevelView<T> L, 
 
 static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128 ? 4 : 0)); }
 
+// Tiled line smoother: a CTA of 8 warps owns 8 consecutive cells of one
+// colour.  Their K-slice systems are gathered with sector-sized row loads
+// into a padded [K][9] shared tile, warp w solves column w by PCR, and the
+// solutions leave through the same tile.
+constexpr int kTileCells = 8;
+template <typename T, int KPL>
+__global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T> L, int color) {
+  constexpr int P = kTileCells + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sd = reinterpret_cast<T*>(smem_raw);  // [S][P] diagonal
+  T* sr = sd + S * P;                      // [S][P] right-hand side, then solution
+  T* st = sr + S * P;                      // [S][P] tau
+  const int sq = L.m * L.m, nc = (int)L.nc;
+  const int j = threadIdx.x % kTileCells, row0 = threadIdx.x / kTileCells;
+  const int rows = blockDim.x / kTileCells;
+  const int cell = blockIdx.x * kTileCells + j;
+  const bool live = cell < sq;
+  i64 nb[3] = {-1, -1, -1};
+  const int c = color * sq + cell;
+  if (live) neighbours(L.m, decode(L.m, c), nb);
+  for (int k = row0; k < S; k += rows) {
+    T dg = 1, rhs = 0, tau = 0;
+    if (live) {
+      const int o = k * nc;
+      tau = L.tau[o + c];
+      dg = 2 * tau;
+      rhs = L.b[o + c];
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        T al = L.alpha[(sl * S + k) * nc + c];
+        dg += al;
+        if (nb[sl] >= 0) rhs += al * L.x[o + (int)nb[sl]];
+      }
+    }
+    sd[k * P + j] = dg;
+    sr[k * P + j] = rhs;
+    st[k * P + j] = tau;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, col = threadIdx.x >> 5;
+  {
+    T a[KPL], d[KPL], cc[KPL], r[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      int k = lane + 32 * q;
+      if (k < S) {
+        T tau = st[k * P + col];
+        d[q] = sd[k * P + col];
+        r[q] = sr[k * P + col];
+        a[q] = (k > 0) ? -tau : (T)0;
+        cc[q] = (k < S - 1) ? -tau : (T)0;
+      } else {
+        d[q] = 1; r[q] = 0; a[q] = 0; cc[q] = 0;
+      }
+    }
+    pcr_solve<T, KPL>(a, d, cc, r, lane);
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      int k = lane + 32 * q;
+      if (k < S) sr[k * P + col] = r[q] / d[q];
+    }
+  }
+  __syncthreads();
+  if (live)
+    for (int k = row0; k < S; k += rows) L.x[k * nc + c] = sr[k * P + j];
+}
+
 template <typename T>
 void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, Stream st) {
   i64 sq = (i64)L.m * L.m;
@@ -227,6 +294,18 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
   prof::begin(id, st);
   if (L.tau) {
     int kpl = pcr_kpl(S);
+    const size_t tile = 3 * (size_t)S * (kTileCells + 1) * sizeof(T);
+    if (kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.nc < (1ll << 31)) {
+      int blocks = (int)((sq + kTileCells - 1) / kTileCells);
+      if (kpl == 1)
+        launch(k_line_pcr_tile_kernel<T, 1>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
+      else if (kpl == 2)
+        launch(k_line_pcr_tile_kernel<T, 2>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
+      else
+        launch(k_line_pcr_tile_kernel<T, 4>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
+      prof::end(id, st, (double)sizeof(T) * 7.0 * (double)S * (double)sq);
+      return;
+    }
     int blocks = (int)std::min<i64>((sq * 32 + kT - 1) / kT, 1 << 20);
     if (kpl == 1)
       launch(k_line_pcr_kernel<T, 1>, blocks, kT, 0, cs(st), S, L, color);
@@ -440,18 +519,19 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
   for (int l = 0; l < g.n; ++l) {
     const LevelView<T>& G = g.L[l];
     const LevelView<T>& V = s.L[l];
-    const i64 n1 = (i64)S_view * G.nc;
-    for (i64 i = threadIdx.x; i < 3 * n1; i += blockDim.x) {
-      int sl = (int)(i / n1);
-      i64 rem = i - (i64)sl * n1;
-      int kv = (int)(rem / G.nc);
-      i64 c = rem - (i64)kv * G.nc;
-      V.alpha[i] = G.alpha[((i64)sl * S + slice0 + kv) * G.nc + c];
+    // per edge slot the S_view staged slices are one contiguous run of n1 values
+    const int nc = (int)G.nc, n1 = S_view * nc;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      const T* src = G.alpha + ((i64)sl * S + slice0) * nc;
+      T* dst = V.alpha + (i64)sl * n1;
+#pragma unroll 4
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) dst[i] = src[i];
     }
     if (G.tau)
-      for (i64 i = threadIdx.x; i < n1; i += blockDim.x) V.tau[i] = G.tau[(i64)slice0 * G.nc + i];
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) V.tau[i] = G.tau[(i64)slice0 * nc + i];
     if (l == 0)
-      for (i64 i = threadIdx.x; i < n1; i += blockDim.x) V.b[i] = G.b[(i64)slice0 * G.nc + i];
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) V.b[i] = G.b[(i64)slice0 * nc + i];
   }
   __syncthreads();
 }
@@ -510,11 +590,38 @@ __global__ void __launch_bounds__(256) k_lap_lower_kernel(int S, LevelSet<T> gls
   for (i64 i = threadIdx.x; i < G0.nc; i += blockDim.x) G0.x[(i64)k * G0.nc + i] = ls.L[0].x[i];
 }
 
+// Walks the flat index i = k nc + c over S nc cells in steps of blockDim.x
+// with one division per thread and level: (k, c) advance by (dk, dc).
+struct SliceWalk {
+  int k, c, dk, dc, nc;
+  __device__ SliceWalk(int nc_) : nc(nc_) {
+    k = threadIdx.x / nc;
+    c = threadIdx.x - k * nc;
+    dk = blockDim.x / nc;
+    dc = blockDim.x - dk * nc;
+  }
+  __device__ void next() {
+    k += dk;
+    c += dc;
+    if (c >= nc) {
+      c -= nc;
+      ++k;
+    }
+  }
+};
+
 // Space-time Schur operator: one CTA for all slices, time lines by warp PCR,
 // all fused levels in shared memory; the coarsest level adds the aggregate
 // correction of k_coarse_kernel.
+// Threads of the fused Schur kernel: 512 where a PCR lane's KPL systems in T
+// would not fit the 64 registers a 1024-thread CTA leaves each thread.
 template <typename T, int KPL>
-__global__ void __launch_bounds__(1024) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
+constexpr int sch_lower_threads() {
+  return sizeof(T) * KPL >= 16 ? 512 : 1024;
+}
+
+template <typename T, int KPL>
+__global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   __shared__ LevelSet<T> ls;
@@ -523,27 +630,23 @@ __global__ void __launch_bounds__(1024) k_sch_lower_kernel(int S, LevelSet<T> gl
   const int last = ls.n - 1;
   for (int l = 0; l < last; ++l) {
     const LevelView<T>& L = ls.L[l];
-    const i64 sq = (i64)L.m * L.m, tot = (i64)S * L.nc;
-    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] = 0;
+    const int sq = L.m * L.m, nc = (int)L.nc, tot = S * nc;
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] = 0;
     __syncthreads();
     for (int it = 0; it < nu; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (i64 w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
+        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
         __syncthreads();
       }
-    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) {
-      int k = (int)(i / L.nc);
-      L.r[i] = L.b[i] - level_apply(S, L, k, i - (i64)k * L.nc);
-    }
+    for (SliceWalk w(nc); w.k < S; w.next()) L.r[w.k * nc + w.c] = L.b[w.k * nc + w.c] - level_apply(S, L, w.k, w.c);
     __syncthreads();
     const LevelView<T>& Lc = ls.L[l + 1];
-    for (i64 i = threadIdx.x; i < (i64)S * Lc.nc; i += blockDim.x) {
-      int k = (int)(i / Lc.nc);
-      i64 C = i - (i64)k * Lc.nc;
+    const int ncc = (int)Lc.nc;
+    for (SliceWalk w(ncc); w.k < S; w.next()) {
       i64 ch[4];
-      children(Lc.m, decode(Lc.m, C), ch);
-      const T* rf = L.r + (i64)k * L.nc;
-      Lc.b[i] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
+      children(Lc.m, decode(Lc.m, w.c), ch);
+      const T* rf = L.r + w.k * nc;
+      Lc.b[w.k * ncc + w.c] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
     }
     __syncthreads();
   }
@@ -552,15 +655,12 @@ __global__ void __launch_bounds__(1024) k_sch_lower_kernel(int S, LevelSet<T> gl
   for (int l = last - 1; l >= 0; --l) {
     const LevelView<T>& L = ls.L[l];
     const LevelView<T>& Lc = ls.L[l + 1];
-    const i64 sq = (i64)L.m * L.m, tot = (i64)S * L.nc;
-    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) {
-      int k = (int)(i / L.nc);
-      L.x[i] += Lc.x[(i64)k * Lc.nc + parent_of(L.m, i - (i64)k * L.nc)];
-    }
+    const int sq = L.m * L.m, nc = (int)L.nc, ncc = (int)Lc.nc;
+    for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * nc + w.c] += Lc.x[w.k * ncc + (int)parent_of(L.m, w.c)];
     __syncthreads();
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
-        for (i64 w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
+        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
         __syncthreads();
       }
   }
@@ -604,13 +704,13 @@ void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int n
   int kpl = pcr_kpl(S);
   if (kpl == 1) {
     set_smem(k_sch_lower_kernel<T, 1>, bytes);
-    launch(k_sch_lower_kernel<T, 1>, 1, 1024, bytes, cs(st), S, ls, nu, nuc);
+    launch(k_sch_lower_kernel<T, 1>, 1, sch_lower_threads<T, 1>(), bytes, cs(st), S, ls, nu, nuc);
   } else if (kpl == 2) {
     set_smem(k_sch_lower_kernel<T, 2>, bytes);
-    launch(k_sch_lower_kernel<T, 2>, 1, 1024, bytes, cs(st), S, ls, nu, nuc);
+    launch(k_sch_lower_kernel<T, 2>, 1, sch_lower_threads<T, 2>(), bytes, cs(st), S, ls, nu, nuc);
   } else if (kpl == 4) {
     set_smem(k_sch_lower_kernel<T, 4>, bytes);
-    launch(k_sch_lower_kernel<T, 4>, 1, 1024, bytes, cs(st), S, ls, nu, nuc);
+    launch(k_sch_lower_kernel<T, 4>, 1, sch_lower_threads<T, 4>(), bytes, cs(st), S, ls, nu, nuc);
   } else {
     throw Error(1, "fused Schur levels need K <= 128");
   }

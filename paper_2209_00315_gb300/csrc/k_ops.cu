@@ -50,11 +50,12 @@ void k_residual(const Dims& d, double mu, const double* phi, const double* rho, 
 }
 
 // ------------------------------------------------------------------ KKT operator
-__global__ void k_slice_mean_kernel(const double* x, i64 n, double* mean) {
+template <typename T>
+__global__ void k_slice_mean_kernel(const T* x, i64 n, T* mean) {
   __shared__ double sm[32];
-  const double* xs = x + (i64)blockIdx.x * n;
+  const T* xs = x + (i64)blockIdx.x * n;
   double a = 0.0;
-  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += xs[i];
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += (double)xs[i];
   a = warp_sum2(a);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sm[w] = a;
@@ -62,12 +63,13 @@ __global__ void k_slice_mean_kernel(const double* x, i64 n, double* mean) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q];
-    mean[blockIdx.x] = t / (double)n;
+    mean[blockIdx.x] = (T)(t / (double)n);
   }
 }
 
-__global__ void k_kkt_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
-                                 const double* xp, const double* xr, const double* xmean, bool with_a, double* y) {
+template <typename T>
+__global__ void k_kkt_phi_kernel(Dims d, const T* phi, const T* rho, const T* r0, const T* r1, const T* xp,
+                                 const T* xr, const T* xmean, bool with_a, T* y) {
   SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi(d, phi, rho, r0, r1, xp, xr, xmean, with_a, jj, c);
 }
 
@@ -102,8 +104,8 @@ void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const doub
   i64 Np = (i64)(d.K + 1) * d.N;
   const double* xr = x + Np;
   prof::begin(prof::KKT, st);
-  launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
-  launch(k_kkt_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
+  launch(k_slice_mean_kernel<double>, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
+  launch(k_kkt_phi_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
   launch(k_kkt_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
   launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, wsum);
   prof::end(prof::KKT, st, 8.0 * (3.0 * Np + 4.0 * d.K * d.Nc));
@@ -135,8 +137,8 @@ void k_kkt_apply_static(const Dims& d, const double* phi, const double* rho, con
   double* xmean = kkt_static_scratch();
   i64 Np = (i64)(d.K + 1) * d.N;
   const double* xr = x + Np;
-  launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
-  launch(k_kkt_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
+  launch(k_slice_mean_kernel<double>, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
+  launch(k_kkt_phi_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
   launch(k_kkt_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
   launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, (double*)nullptr);
 }
@@ -144,36 +146,38 @@ void k_kkt_apply_static(const Dims& d, const double* phi, const double* rho, con
 void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_phi, double* yr_mean, Stream st) {
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);
-  launch(k_slice_mean_kernel, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
-  launch(k_kkt_phi_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, nullptr, nullptr, nullptr, nullptr, yr, yr_mean, false,
+  launch(k_slice_mean_kernel<double>, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
+  launch(k_kkt_phi_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, nullptr, nullptr, nullptr, nullptr, yr, yr_mean, false,
                                                  out_phi);
   prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc));
 }
 
 // ------------------------------------------------------------------ Schur operator
-__global__ void k_schur_u_kernel(Dims d, const double* phi, const double* z, double* u) {
+template <typename T>
+__global__ void k_schur_u_kernel(Dims d, const T* phi, const T* z, T* u) {
   SLICE_LOOP(jj, d.K + 1, c, d.N) u[(i64)jj * d.N + c] = schur_u(d, phi, z, jj, c);
 }
 
-__global__ void k_schur_out_kernel(Dims d, const double* phi, const double* rho, const double* s, const double* u,
-                                   const double* z, double* out) {
+template <typename T>
+__global__ void k_schur_out_kernel(Dims d, const T* phi, const T* rho, const T* s, const T* u, const T* z, T* out) {
   SLICE_LOOP(k0, d.K, C, d.Nc) out[(i64)k0 * d.Nc + C] = schur_out(d, phi, rho, s, u, z, k0, C);
 }
 
 void k_schur_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* z,
                    double* out, double* u, Stream st) {
   prof::begin(prof::SCHUR, st);
-  launch(k_schur_u_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, z, u);
-  launch(k_schur_out_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, u, z, out);
+  launch(k_schur_u_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, z, u);
+  launch(k_schur_out_kernel<double>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, u, z, out);
   prof::end(prof::SCHUR, st, 8.0 * ((double)(d.K + 1) * d.N + 4.0 * d.K * d.Nc));
 }
 
-__global__ void k_atilde_kernel(Dims d, const double* rho, const double* z, double* y) {
-  SLICE_LOOP(k0, d.K, C, d.Nc) y[(i64)k0 * d.Nc + C] = apply_atilde(d, rho, z, k0, C) / d.area_c;
+template <typename T>
+__global__ void k_atilde_kernel(Dims d, const T* rho, const T* z, T* y) {
+  SLICE_LOOP(k0, d.K, C, d.Nc) y[(i64)k0 * d.Nc + C] = apply_atilde(d, rho, z, k0, C) / (T)d.area_c;
 }
 
 void k_atilde_minv(const Dims& d, const double* rho, const double* z, double* y, Stream st) {
-  launch(k_atilde_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, rho, z, y);
+  launch(k_atilde_kernel<double>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, rho, z, y);
 }
 
 // ------------------------------------------------------------------ cost and dual value
@@ -401,4 +405,53 @@ __global__ void k_adj_grad_kernel(Dims d, const double* phi, const double* lam, 
 void k_adjoint_grad(const Dims& d, const double* phi, const double* lam, double* gin, double* gf, Stream st) {
   launch(k_adj_grad_kernel, nblk(d.Nc), kT, 0, cs(st), d, phi, lam, gin, gf);
 }
+}  // namespace ot
+
+namespace ot {
+// ---- FP32 versions of the preconditioner's operators (mixed precision).
+void k_bt_apply(const Dims& d, const float* phi, const float* yr, float* out_phi, float* yr_mean, Stream st) {
+  i64 Np = (i64)(d.K + 1) * d.N;
+  prof::begin(prof::BT, st);
+  launch(k_slice_mean_kernel<float>, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
+  launch(k_kkt_phi_kernel<float>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, (const float*)nullptr,
+         (const float*)nullptr, (const float*)nullptr, (const float*)nullptr, yr, (const float*)yr_mean, false, out_phi);
+  prof::end(prof::BT, st, 4.0 * (2.0 * Np + (double)d.K * d.Nc));
+}
+
+void k_schur_apply(const Dims& d, const float* phi, const float* rho, const float* s, const float* z, float* out,
+                   float* u, Stream st) {
+  prof::begin(prof::SCHUR, st);
+  launch(k_schur_u_kernel<float>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, z, u);
+  launch(k_schur_out_kernel<float>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, (const float*)u, z, out);
+  prof::end(prof::SCHUR, st, 4.0 * ((double)(d.K + 1) * d.N + 4.0 * d.K * d.Nc));
+}
+
+void k_atilde_minv(const Dims& d, const float* rho, const float* z, float* y, Stream st) {
+  launch(k_atilde_kernel<float>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, rho, z, y);
+}
+
+template <typename A, typename B>
+__global__ void k_convert_kernel(const A* x, B* y, i64 n, double scale) {
+  GRID_LOOP(i, n) y[i] = (B)(scale * (double)x[i]);
+}
+void k_convert(const double* x, float* y, i64 n, double scale, Stream st) {
+  launch(k_convert_kernel<double, float>, nblk(n), kT, 0, cs(st), x, y, n, scale);
+}
+void k_convert(const float* x, double* y, i64 n, double scale, Stream st) {
+  launch(k_convert_kernel<float, double>, nblk(n), kT, 0, cs(st), x, y, n, scale);
+}
+
+// out (float) = scale * a (float) .* b (double)
+__global__ void k_mul_mixed_kernel(const float* a, const double* b, double scale, float* out, i64 n) {
+  GRID_LOOP(i, n) out[i] = (float)(scale * (double)a[i] * b[i]);
+}
+void k_mul(const float* a, const double* b, double scale, float* out, i64 n, Stream st) {
+  launch(k_mul_mixed_kernel, nblk(n), kT, 0, cs(st), a, b, scale, out, n);
+}
+
+// y (float) = (float) c - y (the B^T P^T term), per element
+__global__ void k_rsub_mixed_kernel(const double* c, float* y, i64 n) {
+  GRID_LOOP(i, n) y[i] = (float)c[i] - y[i];
+}
+void k_rsub(const double* c, float* y, i64 n, Stream st) { launch(k_rsub_mixed_kernel, nblk(n), kT, 0, cs(st), c, y, n); }
 }  // namespace ot

@@ -90,6 +90,19 @@ void k_scale(const double* x, double a, double* y, i64 n, Stream s);
 void k_fill(double* x, double v, i64 n, Stream s);
 size_t k_reduce_scratch(int nv);  // doubles needed by `partial`
 
+// FP32 overloads (mixed precision: the preconditioner's inner Krylov solve).
+// Per-thread accumulation is in float; cross-thread reductions and the
+// scalars (h, y, out, partial) are double.
+void k_slice_sums(const float* x, int S, i64 n, double scale, float* sums, Stream s);
+void k_slice_shift(float* x, int S, i64 n, const float* sums, double scale, Stream s);
+void k_mdot(const float* V, i64 ld, int nv, const float* w, i64 n, double* out, double* partial, Stream s);
+void k_mupdate(const float* V, i64 ld, int nv, const double* h, float* w, i64 n, double* out, bool dots,
+               bool norm, double* partial, Stream s);
+void k_mcombine(const float* Z, i64 ld, int nv, const double* y, float* x, i64 n, Stream s);
+void k_dot(const float* x, const float* y, i64 n, double* out, double* partial, Stream s);
+void k_scale_by_inv_norm(const float* x, const double* nrm2, float* y, i64 n, Stream s);
+void k_scale(const float* x, double a, float* y, i64 n, Stream s);
+
 // ------------------------------------------------------------------ operators (FP64)
 void k_residual(const Dims& d, double mu, const double* phi, const double* rho, const double* s,
                 const double* r0, const double* r1, double* Fphi, double* Frho, double* Fs, Stream st);
@@ -140,6 +153,18 @@ void k_adjoint_rhs(const Dims& d, const double* phi, const double* rho, const do
                    double* rhs, double* gsum, Stream st);
 // grad_in, grad_f (N' each) from the adjoint potential lam ((K+1) x N).
 void k_adjoint_grad(const Dims& d, const double* phi, const double* lam, double* gin, double* gf, Stream st);
+// FP32 versions of the Schur-side operators (mixed precision), same layouts.
+void k_bt_apply(const Dims& d, const float* phi, const float* yr, float* out_phi, float* yr_mean, Stream st);
+void k_schur_apply(const Dims& d, const float* phi, const float* rho, const float* s, const float* z, float* out,
+                   float* u, Stream st);
+void k_atilde_minv(const Dims& d, const float* rho, const float* z, float* y, Stream st);
+// dst = scale * src, converting precision
+void k_convert(const double* src, float* dst, i64 n, double scale, Stream st);
+void k_convert(const float* src, double* dst, i64 n, double scale, Stream st);
+// out = (float)(scale * a .* b)
+void k_mul(const float* a, const double* b, double scale, float* out, i64 n, Stream st);
+// y = c - y
+void k_rsub(const double* c, float* y, i64 n, Stream st);
 // max |x| and non-finite flag: out[0] = max|x|, out[1] = 1 if any non-finite
 void k_absmax(const double* x, i64 n, double* out, double* partial, Stream st);
 // min(x) -> out[0]

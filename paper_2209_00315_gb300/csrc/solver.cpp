@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <functional>
+#include <type_traits>
 #include <vector>
 
 namespace ot {
@@ -76,27 +77,32 @@ void Hierarchy<T>::release() {
 template struct Hierarchy<float>;
 template struct Hierarchy<double>;
 
-void Krylov::build(int m, i64 n_) {
+template <typename T>
+void KrylovT<T>::build(int m, i64 n_) {
   release();
   mmax = m;
   n = n_;
-  V = (double*)dev::alloc(sizeof(double) * (size_t)(m + 1) * n);
-  Z = (double*)dev::alloc(sizeof(double) * (size_t)m * n);
-  w = (double*)dev::alloc(sizeof(double) * (size_t)n);
+  V = (T*)dev::alloc(sizeof(T) * (size_t)(m + 1) * n);
+  Z = (T*)dev::alloc(sizeof(T) * (size_t)m * n);
+  w = (T*)dev::alloc(sizeof(T) * (size_t)n);
   hc1 = (double*)dev::alloc(sizeof(double) * (m + 2));
   hc2 = (double*)dev::alloc(sizeof(double) * (m + 2));
   y = (double*)dev::alloc(sizeof(double) * (m + 2));
 }
 
-void Krylov::release() {
+template <typename T>
+void KrylovT<T>::release() {
   dev::release(V);
   dev::release(Z);
   dev::release(w);
   dev::release(hc1);
   dev::release(hc2);
   dev::release(y);
-  V = Z = w = hc1 = hc2 = y = nullptr;
+  V = Z = w = nullptr;
+  hc1 = hc2 = y = nullptr;
 }
+template struct KrylovT<float>;
+template struct KrylovT<double>;
 
 static double* dalloc(i64 n) { return (double*)dev::alloc(sizeof(double) * (size_t)(n > 0 ? n : 1)); }
 
@@ -135,11 +141,46 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
     cur_restart = opt.fgmres_restart;
     cur_inner = opt.schur_max_iter;
     outer.build(cur_restart, ntot);
-    inner.build(cur_inner, Nr);
     if (prec == OT_PREC_MIXED) {
+      innerf.build(cur_inner, Nr);
+      // phi, u, bphi: Np each; rho, s, srhs, zeta, y: Nr each; mean, sums: K+2 each
+      const i64 nf = 3 * Np + 5 * Nr + 2 * (K + 2);
+      f32 = (float*)dev::alloc(sizeof(float) * (size_t)nf);
+      float* p = f32;
+      auto take = [&](i64 len) {
+        float* q = p;
+        p += len;
+        return q;
+      };
+      phif = take(Np);
+      rhof = take(Nr);
+      sf = take(Nr);
+      bbf.phi = phif;
+      bbf.rho = rhof;
+      bbf.s = sf;
+      bbf.u = take(Np);
+      bbf.bphi = take(Np);
+      bbf.srhs = take(Nr);
+      bbf.zeta = take(Nr);
+      bbf.y = take(Nr);
+      bbf.mean = take(K + 2);
+      bbf.sums = take(K + 2);
+      bbf.K = &innerf;
       lapf.build(d.m, K + 1, false);
       schf.build(d.n, K, true);
     } else {
+      inner.build(cur_inner, Nr);
+      bbd.phi = phi;
+      bbd.rho = rho;
+      bbd.s = s;
+      bbd.u = u;
+      bbd.bphi = bphi;
+      bbd.srhs = srhs;
+      bbd.zeta = zeta;
+      bbd.y = nullptr;
+      bbd.mean = xmean;
+      bbd.sums = scal + 64;
+      bbd.K = &inner;
       lapd.build(d.m, K + 1, false);
       schd.build(d.n, K, true);
     }
@@ -158,6 +199,9 @@ Workspace::~Workspace() {
   gsum = wsum = cshift = xmean = mass = scal = partial = u = bphi = srhs = zeta = nullptr;
   outer.release();
   inner.release();
+  innerf.release();
+  dev::release(f32);
+  f32 = phif = rhof = sf = nullptr;
   lapf.release();
   schf.release();
   lapd.release();
@@ -193,13 +237,16 @@ static void vcycle(Hierarchy<T>& H, size_t l, int nu, int nuc, Stream st) {
   }
 }
 
-// x ~= M^{-1} b by `cycles` V-cycles from zero (b, x in FP64; the cycle in T).
-template <typename T>
-static void mg_solve(Hierarchy<T>& H, const double* b, double* x, int cycles, int nu, int nuc, Stream st) {
+// x ~= M^{-1} b by `cycles` V-cycles from zero (x in FP64; b in FP64 or T; the cycle in T).
+template <typename T, typename In>
+static void mg_solve(Hierarchy<T>& H, const In* b, double* x, int cycles, int nu, int nuc, Stream st) {
   LevelView<T>& L = H.lv[0];
   i64 n = (i64)H.S * L.nc;
   size_t bytes = sizeof(T) * (size_t)n;
-  k_mg_load<T>(b, 1.0, L.b, nullptr, n, st);
+  if constexpr (std::is_same<In, T>::value)
+    dev::copy_d2d(L.b, b, bytes, st);
+  else
+    k_mg_load<T>(b, 1.0, L.b, nullptr, n, st);
   if (cycles <= 1) {
     vcycle(H, 0, nu, nuc, st);
     k_mg_store<T>(L.x, x, n, st);
@@ -219,6 +266,22 @@ static void mg_solve(Hierarchy<T>& H, const double* b, double* x, int cycles, in
   k_mg_store<T>(H.acc, x, n, st);
 }
 
+// x ~= M^{-1} b by one V-cycle, b and x in T: level 0 works on b and x in place.
+template <typename T>
+static void mg_apply(Hierarchy<T>& H, const T* b, T* x, int nu, int nuc, Stream st) {
+  struct Swap {
+    LevelView<T>& L;
+    T *b0, *x0;
+    ~Swap() {
+      L.b = b0;
+      L.x = x0;
+    }
+  } guard{H.lv[0], H.lv[0].b, H.lv[0].x};
+  H.lv[0].b = const_cast<T*>(b);  // read only
+  H.lv[0].x = x;
+  vcycle(H, 0, nu, nuc, st);
+}
+
 template <typename T>
 static void refresh_t(Workspace& W, Hierarchy<T>& lap, Hierarchy<T>& sch, Stream st) {
   k_mg_lap_coef0<T>(W.d, W.rho, W.r0, W.r1, lap.lv[0].alpha, st);
@@ -228,21 +291,26 @@ static void refresh_t(Workspace& W, Hierarchy<T>& lap, Hierarchy<T>& sch, Stream
 }
 
 void refresh_coefficients(Workspace& W, Stream st) {
-  if (W.precision == OT_PREC_MIXED)
+  if (W.precision == OT_PREC_MIXED) {
     refresh_t(W, W.lapf, W.schf, st);
-  else
+    k_convert(W.phi, W.phif, W.Np, 1.0, st);
+    k_convert(W.rho, W.rhof, W.Nr, 1.0, st);
+    k_convert(W.s, W.sf, W.Nr, 1.0, st);
+  } else
     refresh_t(W, W.lapd, W.schd, st);
 }
 
 // ------------------------------------------------------------------ Arnoldi
-typedef std::function<void(const double*, double*)> OpFn;
+template <typename T>
+using OpFn = std::function<void(const T*, T*)>;
 
 // One restart cycle of right-preconditioned flexible GMRES.  K.V[0] holds the
 // normalised residual, beta its norm.  Classical Gram-Schmidt with one
 // reorthogonalisation on the device; Givens rotations on the host.  On return
 // x += Z y and *res is the residual estimate; returns the number of steps.
-static int arnoldi(Workspace& W, Krylov& K, int m, double beta, double tol_abs, const OpFn& prec, const OpFn& op,
-                   double* x, double* res, Stream st) {
+template <typename T>
+static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_abs, const OpFn<T>& prec,
+                   const OpFn<T>& op, T* x, double* res, Stream st) {
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 1.0), sn(m, 0.0), g(m + 1, 0.0);
   auto h = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
   g[0] = beta;
@@ -250,8 +318,8 @@ static int arnoldi(Workspace& W, Krylov& K, int m, double beta, double tol_abs, 
   int j = 0;
   double* hb = W.host;
   for (j = 0; j < m;) {
-    double* vj = K.V + (i64)j * K.n;
-    double* zj = K.Z + (i64)j * K.n;
+    T* vj = K.V + (i64)j * K.n;
+    T* zj = K.Z + (i64)j * K.n;
     prec(vj, zj);
     op(zj, K.w);
     k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
@@ -296,7 +364,8 @@ static int arnoldi(Workspace& W, Krylov& K, int m, double beta, double tol_abs, 
   return k;
 }
 
-static double norm2(Workspace& W, const double* x, i64 n, Stream st) {
+template <typename T>
+static double norm2(Workspace& W, const T* x, i64 n, Stream st) {
   k_dot(x, x, n, W.scal + 32, W.partial, st);
   dev::copy_d2h(W.host + 1000, W.scal + 32, sizeof(double), st);
   dev::sync(st);
@@ -304,52 +373,62 @@ static double norm2(Workspace& W, const double* x, i64 n, Stream st) {
 }
 
 // ------------------------------------------------------------------ BB preconditioner
+// Inner solve of the Schur system to relative tolerance eps_schur, GMRES
+// preconditioned by one space-time V-cycle; vectors in T.
 template <typename T>
-static void inner_solve(Workspace& W, const ot_options& opt, Hierarchy<T>& sch, const double* b, double* x,
-                        Stream st) {
-  Krylov& K = W.inner;
+static void inner_solve(Workspace& W, const ot_options& opt, Hierarchy<T>& sch, const BBVectors<T>& B, const T* b,
+                        T* x, Stream st) {
+  KrylovT<T>& K = *B.K;
   i64 n = W.Nr;
-  dev::zero(x, sizeof(double) * (size_t)n, st);
+  dev::zero(x, sizeof(T) * (size_t)n, st);
   double beta = norm2(W, b, n, st);
   if (beta == 0.0) return;
   k_scale(b, 1.0 / beta, K.V, n, st);
-  OpFn prec = [&](const double* in, double* out) {
-    mg_solve(sch, in, out, 1, opt.smooth_sweeps, opt.coarse_sweeps, st);
-  };
-  OpFn op = [&](const double* in, double* out) { k_schur_apply(W.d, W.phi, W.rho, W.s, in, out, W.u, st); };
+  OpFn<T> prec = [&](const T* in, T* out) { mg_apply(sch, in, out, opt.smooth_sweeps, opt.coarse_sweeps, st); };
+  OpFn<T> op = [&](const T* in, T* out) { k_schur_apply(W.d, B.phi, B.rho, B.s, in, out, B.u, st); };
   double res = 0.0;
   int its = arnoldi(W, K, std::min(opt.schur_max_iter, K.mmax), beta, opt.eps_schur * beta, prec, op, x, &res, st);
   W.inner_iters += its;
 }
 
+// out = P_BB^{-1} v with v = (c; d) and out = (x; y) in FP64; the solves in T.
 template <typename T>
-static void bb_apply_t(Workspace& W, const ot_options& opt, Hierarchy<T>& lap, Hierarchy<T>& sch, const double* v,
-                       double* out, Stream st) {
+static void bb_apply_t(Workspace& W, const ot_options& opt, Hierarchy<T>& lap, Hierarchy<T>& sch,
+                       const BBVectors<T>& B, const double* v, double* out, Stream st) {
+  constexpr bool f64 = std::is_same<T, double>::value;
   const Dims& d = W.d;
   const double* c = v;
   const double* dv = v + W.Np;
   double* x = out;
   double* y = out + W.Np;
   // Schur system (Eq. pseudoschur-bis): (Diag(s) A~ - Diag(rho) B M^-1 B~) z = -Diag(rho) d
-  k_mul(W.rho, dv, -1.0, W.srhs, W.Nr, st);
-  inner_solve(W, opt, sch, W.srhs, W.zeta, st);
+  k_mul(B.rho, dv, -1.0, B.srhs, W.Nr, st);
+  inner_solve(W, opt, sch, B, B.srhs, B.zeta, st);
   // y = M'^{-1} A~ z
-  k_atilde_minv(d, W.rho, W.zeta, y, st);
+  T* yt = nullptr;
+  if constexpr (f64)
+    yt = y;
+  else
+    yt = B.y;
+  k_atilde_minv(d, B.rho, B.zeta, yt, st);
+  if constexpr (!f64) k_convert(yt, y, W.Nr, 1.0, st);
   // b = c - B^T P^T y, kept in the range of A (zero slice sums)
-  k_bt_apply(d, W.phi, y, W.bphi, W.xmean, st);
-  k_axpby(1.0, c, -1.0, W.bphi, W.Np, st);
-  double* sm = W.scal + 64;
-  k_slice_sums(W.bphi, d.K + 1, d.N, 1.0 / (double)d.N, sm, st);
-  k_slice_shift(W.bphi, d.K + 1, d.N, sm, 1.0, st);
+  k_bt_apply(d, B.phi, yt, B.bphi, B.mean, st);
+  if constexpr (f64)
+    k_axpby(1.0, c, -1.0, B.bphi, W.Np, st);
+  else
+    k_rsub(c, B.bphi, W.Np, st);
+  k_slice_sums(B.bphi, d.K + 1, d.N, 1.0 / (double)d.N, B.sums, st);
+  k_slice_shift(B.bphi, d.K + 1, d.N, B.sums, 1.0, st);
   // A^j x^j = b^j, j = 1..K+1, by multigrid (Eq. x-triang)
-  mg_solve(lap, W.bphi, x, opt.lap_cycles, opt.smooth_sweeps, opt.coarse_sweeps, st);
+  mg_solve(lap, (const T*)B.bphi, x, opt.lap_cycles, opt.smooth_sweeps, opt.coarse_sweeps, st);
 }
 
 void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st) {
   if (W.precision == OT_PREC_MIXED)
-    bb_apply_t(W, opt, W.lapf, W.schf, v, out, st);
+    bb_apply_t(W, opt, W.lapf, W.schf, W.bbf, v, out, st);
   else
-    bb_apply_t(W, opt, W.lapd, W.schd, v, out, st);
+    bb_apply_t(W, opt, W.lapd, W.schd, W.bbd, v, out, st);
 }
 
 // ------------------------------------------------------------------ FGMRES
@@ -360,8 +439,8 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   double beta = norm2(W, b, n, st);
   if (beta <= tol_abs) return beta;
   k_scale(b, 1.0 / beta, K.V, n, st);
-  OpFn prec = [&](const double* in, double* out) { bb_apply(W, opt, in, out, st); };
-  OpFn op = [&](const double* in, double* out) {
+  OpFn<double> prec = [&](const double* in, double* out) { bb_apply(W, opt, in, out, st); };
+  OpFn<double> op = [&](const double* in, double* out) {
     k_kkt_apply(W.d, W.phi, W.rho, W.s, W.r0, W.r1, in, out, W.xmean, nullptr, st);
   };
   int total = 0;

@@ -24,18 +24,37 @@ struct Hierarchy {
   bool built() const { return !lv.empty(); }
 };
 
-// Krylov basis storage for one (F)GMRES solver.
-struct Krylov {
+// Krylov basis storage for one (F)GMRES solver; the basis in T, the
+// Hessenberg columns and coefficients in double.
+template <typename T>
+struct KrylovT {
   int mmax = 0;
   i64 n = 0;
-  double* V = nullptr;     // (mmax+1) x n
-  double* Z = nullptr;     // mmax x n
-  double* w = nullptr;     // n
+  T* V = nullptr;          // (mmax+1) x n
+  T* Z = nullptr;          // mmax x n
+  T* w = nullptr;          // n
   double* hc1 = nullptr;   // mmax+2
   double* hc2 = nullptr;   // mmax+2
   double* y = nullptr;     // mmax
   void build(int m, i64 n);
   void release();
+};
+typedef KrylovT<double> Krylov;
+
+// The BB preconditioner's vectors in the precision T of its Schur solve.  For
+// T = double the state pointers alias the FP64 state; for T = float they are
+// copies refreshed with the coefficients once per Newton step.
+template <typename T>
+struct BBVectors {
+  const T *phi = nullptr, *rho = nullptr, *s = nullptr;
+  T* u = nullptr;       // Schur scratch, (K+1) N
+  T* srhs = nullptr;    // Nr
+  T* zeta = nullptr;    // Nr
+  T* y = nullptr;       // Nr (T = float only: y before conversion)
+  T* bphi = nullptr;    // Np
+  T* mean = nullptr;    // K+2
+  T* sums = nullptr;    // K+2
+  KrylovT<T>* K = nullptr;
 };
 
 // Everything one (mesh, K, precision) needs on the device.
@@ -54,6 +73,11 @@ struct Workspace {
   // BB
   double *u = nullptr, *bphi = nullptr, *srhs = nullptr, *zeta = nullptr;
   Krylov outer, inner;
+  KrylovT<float> innerf;
+  float* f32 = nullptr;       // one allocation for the FP32 vectors of mixed precision
+  float *phif = nullptr, *rhof = nullptr, *sf = nullptr;
+  BBVectors<double> bbd;
+  BBVectors<float> bbf;
   Hierarchy<float> lapf, schf;
   Hierarchy<double> lapd, schd;
   double* host = nullptr;     // pinned host scratch (256 doubles)

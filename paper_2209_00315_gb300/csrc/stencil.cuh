@@ -138,13 +138,15 @@ OT_HD void children(int n, const Cell& q, i64 ch[4]) {
 }
 
 // rho^k for k = 0..K+1 (paper index): boundary data at k = 0 and k = K+1.
-OT_HD double rho_at(const Dims& d, const double* rho, const double* r0, const double* r1, int k, i64 C) {
+template <typename T>
+OT_HD T rho_at(const Dims& d, const T* rho, const T* r0, const T* r1, int k, i64 C) {
   return k == 0 ? r0[C] : (k == d.K + 1 ? r1[C] : rho[(i64)(k - 1) * d.Nc + C]);
 }
 
 // Mean density of phi slice jj (paper j = jj+1) on coarse cell C: (rho^{j-1} + rho^j)/2.
-OT_HD double rho_bar(const Dims& d, const double* rho, const double* r0, const double* r1, int jj, i64 C) {
-  return 0.5 * (rho_at(d, rho, r0, r1, jj, C) + rho_at(d, rho, r0, r1, jj + 1, C));
+template <typename T>
+OT_HD T rho_bar(const Dims& d, const T* rho, const T* r0, const T* r1, int jj, i64 C) {
+  return (T)0.5 * (rho_at(d, rho, r0, r1, jj, C) + rho_at(d, rho, r0, r1, jj + 1, C));
 }
 
 // ----------------------------------------------------------------- residual
@@ -203,32 +205,33 @@ OT_HD double residual_rho(const Dims& d, const double* phi, const double* s, int
 // phi rows of [A, B^T P^T] x, phi slice jj (paper j = jj+1), with y = P^T x_rho (slice means xmean removed):
 //   sum_e T_e [rho~^j_e (x_c - x_o) + (ybar^j_Pc + ybar^j_Po)/2 (phi_c - phi_o)] + |c| (y^{j-1} - y^j)_Pc/dt,
 //   ybar^j = (y^{j-1} + y^j)/2, y^0 = y^{K+1} = 0.  with_a = false drops the A term.
-OT_HD double kkt_phi(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
-                     const double* xp, const double* xr, const double* xmean, bool with_a, int jj, i64 c) {
+template <typename T>
+OT_HD T kkt_phi(const Dims& d, const T* phi, const T* rho, const T* r0, const T* r1,
+                     const T* xp, const T* xr, const T* xmean, bool with_a, int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
   Cell nq[3];
   neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
-  const double* ph = phi + (i64)jj * d.N;
-  const double* xs = xp + (i64)jj * d.N;
-  const double* ym = (jj >= 1) ? xr + (i64)(jj - 1) * d.Nc : nullptr;
-  const double* yp = (jj <= d.K - 1) ? xr + (i64)jj * d.Nc : nullptr;
-  double mm = (jj >= 1) ? xmean[jj - 1] : 0.0, mp = (jj <= d.K - 1) ? xmean[jj] : 0.0;
-  double yma = ym ? ym[P] - mm : 0.0, ypa = yp ? yp[P] - mp : 0.0;
-  double acc = d.area_f * (yma - ypa) / d.dt;
-  double ybc = 0.5 * (yma + ypa);
-  double rc = with_a ? rho_bar(d, rho, r0, r1, jj, P) : 0.0;
-  double pc = ph[c], xc = with_a ? xs[c] : 0.0;
+  const T* ph = phi + (i64)jj * d.N;
+  const T* xs = xp + (i64)jj * d.N;
+  const T* ym = (jj >= 1) ? xr + (i64)(jj - 1) * d.Nc : nullptr;
+  const T* yp = (jj <= d.K - 1) ? xr + (i64)jj * d.Nc : nullptr;
+  T mm = (jj >= 1) ? xmean[jj - 1] : (T)0, mp = (jj <= d.K - 1) ? xmean[jj] : (T)0;
+  T yma = ym ? ym[P] - mm : (T)0, ypa = yp ? yp[P] - mp : (T)0;
+  T acc = (T)d.area_f * (yma - ypa) / (T)d.dt;
+  T ybc = (T)0.5 * (yma + ypa);
+  T rc = with_a ? rho_bar(d, rho, r0, r1, jj, P) : (T)0;
+  T pc = ph[c], xc = with_a ? xs[c] : (T)0;
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
     i64 o = nb[sl];
     i64 Po = parent(d.m, nq[sl]);
-    double ybo = 0.5 * ((ym ? ym[Po] - mm : 0.0) + (yp ? yp[Po] - mp : 0.0));
-    double term = 0.5 * (ybc + ybo) * (pc - ph[o]);
-    if (with_a) term += 0.5 * (rc + rho_bar(d, rho, r0, r1, jj, Po)) * (xc - xs[o]);
-    acc += trans(sl) * term;
+    T ybo = (T)0.5 * ((ym ? ym[Po] - mm : (T)0) + (yp ? yp[Po] - mp : (T)0));
+    T term = (T)0.5 * (ybc + ybo) * (pc - ph[o]);
+    if (with_a) term += (T)0.5 * (rc + rho_bar(d, rho, r0, r1, jj, Po)) * (xc - xs[o]);
+    acc += (T)trans(sl) * term;
   }
   return acc;
 }
@@ -236,15 +239,16 @@ OT_HD double kkt_phi(const Dims& d, const double* phi, const double* rho, const 
 // (B x)^k on coarse cell C, rho slice k0 = k-1 (Sec. 3, B = J^T D_t M + H G D_x):
 //   sum_{c in C} [ |c| (x^{k+1} - x^k)_c/dt
 //                  + 1/4 sum_e T_e ((phi^k_c - phi^k_o)(x^k_c - x^k_o) + (same at k+1)) ].
-OT_HD double apply_B(const Dims& d, const double* phi, const double* x, int k0, i64 C) {
+template <typename T>
+OT_HD T apply_B(const Dims& d, const T* phi, const T* x, int k0, i64 C) {
   Cell qc = decode(d.n, C);
   i64 ch[4];
   children(d.n, qc, ch);
-  const double* p0 = phi + (i64)k0 * d.N;
-  const double* p1 = p0 + d.N;
-  const double* x0 = x + (i64)k0 * d.N;
-  const double* x1 = x0 + d.N;
-  double acc = 0.0;
+  const T* p0 = phi + (i64)k0 * d.N;
+  const T* p1 = p0 + d.N;
+  const T* x0 = x + (i64)k0 * d.N;
+  const T* x1 = x0 + d.N;
+  T acc = (T)0;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     i64 c = ch[a];
@@ -252,70 +256,74 @@ OT_HD double apply_B(const Dims& d, const double* phi, const double* x, int k0, 
     i64 nb[3];
     Cell nq[3];
     neighbours(d.m, q, nb, nq);
-    acc += d.area_f * (x1[c] - x0[c]) / d.dt;
+    acc += (T)d.area_f * (x1[c] - x0[c]) / (T)d.dt;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
       if (nb[sl] < 0) continue;
       i64 o = nb[sl];
-      acc += 0.25 * trans(sl) * ((p0[c] - p0[o]) * (x0[c] - x0[o]) + (p1[c] - p1[o]) * (x1[c] - x1[o]));
+      acc += (T)0.25 * (T)trans(sl) * ((p0[c] - p0[o]) * (x0[c] - x0[o]) + (p1[c] - p1[o]) * (x1[c] - x1[o]));
     }
   }
   return acc;
 }
 
 // rho rows before projection: w = B x_phi - C P^T x_rho, C = M' diag(s/rho).
-OT_HD double kkt_rho(const Dims& d, const double* phi, const double* rho, const double* s, const double* xp,
-                     const double* xr, const double* xmean, int k0, i64 C) {
+template <typename T>
+OT_HD T kkt_rho(const Dims& d, const T* phi, const T* rho, const T* s, const T* xp,
+                     const T* xr, const T* xmean, int k0, i64 C) {
   i64 idx = (i64)k0 * d.Nc + C;
-  double xh = xr[idx] - xmean[k0];
-  return apply_B(d, phi, xp, k0, C) - d.area_c * s[idx] / rho[idx] * xh;
+  T xh = xr[idx] - xmean[k0];
+  return apply_B(d, phi, xp, k0, C) - (T)d.area_c * s[idx] / rho[idx] * xh;
 }
 
 // ----------------------------------------------------------------- BB pieces
 // u = M^{-1} B~ z on fine cell c, phi slice jj (paper j = jj+1), reading of Sec. 4.3.2:
 //   (z^j - z^{j-1})_Pc/dt + 1/(2|c|) sum_e T_e (phi^j_c - phi^j_o)(zbar^j_Pc - zbar^j_Po),
 //   zbar^j = (z^{j-1} + z^j)/2, z^0 = z^{K+1} = 0.
-OT_HD double schur_u(const Dims& d, const double* phi, const double* z, int jj, i64 c) {
+template <typename T>
+OT_HD T schur_u(const Dims& d, const T* phi, const T* z, int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
   Cell nq[3];
   neighbours(d.m, q, nb, nq);
   i64 P = parent(d.m, q);
-  const double* ph = phi + (i64)jj * d.N;
-  const double* zm = (jj >= 1) ? z + (i64)(jj - 1) * d.Nc : nullptr;
-  const double* zp = (jj <= d.K - 1) ? z + (i64)jj * d.Nc : nullptr;
-  double zmc = zm ? zm[P] : 0.0, zpc = zp ? zp[P] : 0.0;
-  double zbc = 0.5 * (zmc + zpc);
-  double acc = 0.0;
+  const T* ph = phi + (i64)jj * d.N;
+  const T* zm = (jj >= 1) ? z + (i64)(jj - 1) * d.Nc : nullptr;
+  const T* zp = (jj <= d.K - 1) ? z + (i64)jj * d.Nc : nullptr;
+  T zmc = zm ? zm[P] : (T)0, zpc = zp ? zp[P] : (T)0;
+  T zbc = (T)0.5 * (zmc + zpc);
+  T acc = (T)0;
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
     i64 Po = parent(d.m, nq[sl]);
-    double zbo = 0.5 * ((zm ? zm[Po] : 0.0) + (zp ? zp[Po] : 0.0));
-    acc += trans(sl) * (ph[c] - ph[nb[sl]]) * (zbc - zbo);
+    T zbo = (T)0.5 * ((zm ? zm[Po] : (T)0) + (zp ? zp[Po] : (T)0));
+    acc += (T)trans(sl) * (ph[c] - ph[nb[sl]]) * (zbc - zbo);
   }
-  return (zpc - zmc) / d.dt + 0.5 * acc / d.area_f;
+  return (zpc - zmc) / (T)d.dt + (T)0.5 * acc / (T)d.area_f;
 }
 
 // (A~^k z)_C on the coarse grid: sum_E T_E (rho^k_C + rho^k_O)/2 (z_C - z_O).
-OT_HD double apply_atilde(const Dims& d, const double* rho, const double* z, int k0, i64 C) {
+template <typename T>
+OT_HD T apply_atilde(const Dims& d, const T* rho, const T* z, int k0, i64 C) {
   Cell q = decode(d.n, C);
   i64 nb[3];
   neighbours(d.n, q, nb);
-  const double* rk = rho + (i64)k0 * d.Nc;
-  const double* zk = z + (i64)k0 * d.Nc;
-  double acc = 0.0;
+  const T* rk = rho + (i64)k0 * d.Nc;
+  const T* zk = z + (i64)k0 * d.Nc;
+  T acc = (T)0;
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
-    acc += trans(sl) * 0.5 * (rk[C] + rk[nb[sl]]) * (zk[C] - zk[nb[sl]]);
+    acc += (T)trans(sl) * (T)0.5 * (rk[C] + rk[nb[sl]]) * (zk[C] - zk[nb[sl]]);
   }
   return acc;
 }
 
 // Schur operator row (Eq. pseudoschur-bis): s (A~ z) - rho (B u) with u = M^{-1} B~ z.
-OT_HD double schur_out(const Dims& d, const double* phi, const double* rho, const double* s, const double* u,
-                       const double* z, int k0, i64 C) {
+template <typename T>
+OT_HD T schur_out(const Dims& d, const T* phi, const T* rho, const T* s, const T* u,
+                       const T* z, int k0, i64 C) {
   i64 idx = (i64)k0 * d.Nc + C;
   return s[idx] * apply_atilde(d, rho, z, k0, C) - rho[idx] * apply_B(d, phi, u, k0, C);
 }

@@ -139,12 +139,13 @@ def test_ipm_matches_oracle_gaussians_8x8(gpu_lib, precision):
 
 
 @pytest.mark.parametrize("n,K,seed", [(6, 3, 1), (10, 5, 2)])
-def test_ipm_matches_oracle_mixtures(gpu_lib, n, K, seed):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ipm_matches_oracle_mixtures(gpu_lib, n, K, seed, precision):
     from ot_inputs import mixture_params
 
     r0 = make_density(n, *mixture_params(seed, 3), 1e-4)
     r1 = make_density(n, *mixture_params(seed + 50, 3), 1e-4)
-    d, res, ref = _ipm_pair(n, K, r0, r1)
+    d, res, ref = _ipm_pair(n, K, r0, r1, precision)
     assert abs(res["cost"] - ref.cost) < 1e-8 * ref.cost
     assert rel(res["rho"], ref.rho) < 1e-6 and rel(res["phi"], ref.phi) < 1e-6
     assert float(res["rho"].min()) > 0 and float(res["s"].min()) > 0
