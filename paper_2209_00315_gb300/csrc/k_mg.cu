@@ -67,18 +67,18 @@ void k_mg_schur_coef0(const Dims& d, const double* phi, const double* rho, const
 template <typename T>
 __global__ void k_restrict_coef_kernel(int S, LevelView<T> f, LevelView<T> c) {
   SLICE_LOOP(k, S, C, c.nc) {
-    i64 i = (i64)k * c.nc + C;
+    i64 i = (i64)k * c.ld + C;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
       i64 src[2];
       coarse_coef_sources(c.m, C, sl, src);
-      const T* af = f.alpha + ((i64)sl * S + k) * f.nc;
-      c.alpha[((i64)sl * S + k) * c.nc + C] = (T)0.5 * (af[src[0]] + af[src[1]]);
+      const T* af = f.alpha + ((i64)sl * S + k) * f.ld;
+      c.alpha[((i64)sl * S + k) * c.ld + C] = (T)0.5 * (af[src[0]] + af[src[1]]);
     }
     if (c.tau) {
       i64 ch[4];
       children(c.m, decode(c.m, C), ch);
-      const T* tf = f.tau + (i64)k * f.nc;
+      const T* tf = f.tau + (i64)k * f.ld;
       c.tau[i] = tf[ch[0]] + tf[ch[1]] + tf[ch[2]] + tf[ch[3]];
     }
   }
@@ -113,36 +113,41 @@ __device__ __forceinline__ void pcr_solve(T (&a)[KPL], T (&d)[KPL], T (&c)[KPL],
 #pragma unroll
   for (int j = 0; j < LOG2; ++j) {
     const int s = 1 << j;
-    T am[KPL], dm[KPL], cm[KPL], rm[KPL], ap[KPL], dp[KPL], cp[KPL], rp[KPL];
+    // each row's 1/d is formed once and travels instead of d: no quotient
+    // inside the elimination (a row beyond either end is the identity row)
+    T iv[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) iv[q] = mg_div((T)1, d[q]);
+    T am[KPL], im[KPL], cm[KPL], rm[KPL], ap[KPL], ip[KPL], cp[KPL], rp[KPL];
     if (s < 32) {
       const int lm = (lane - s) & 31, lp = (lane + s) & 31;
-      T xa[KPL], xd[KPL], xc[KPL], xr[KPL], ya[KPL], yd[KPL], yc[KPL], yr[KPL];
+      T xa[KPL], xi[KPL], xc[KPL], xr[KPL], ya[KPL], yi[KPL], yc[KPL], yr[KPL];
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         xa[q] = __shfl_sync(0xffffffffu, a[q], lm);
-        xd[q] = __shfl_sync(0xffffffffu, d[q], lm);
+        xi[q] = __shfl_sync(0xffffffffu, iv[q], lm);
         xc[q] = __shfl_sync(0xffffffffu, c[q], lm);
         xr[q] = __shfl_sync(0xffffffffu, r[q], lm);
         ya[q] = __shfl_sync(0xffffffffu, a[q], lp);
-        yd[q] = __shfl_sync(0xffffffffu, d[q], lp);
+        yi[q] = __shfl_sync(0xffffffffu, iv[q], lp);
         yc[q] = __shfl_sync(0xffffffffu, c[q], lp);
         yr[q] = __shfl_sync(0xffffffffu, r[q], lp);
       }
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         if (lane >= s) {
-          am[q] = xa[q]; dm[q] = xd[q]; cm[q] = xc[q]; rm[q] = xr[q];
+          am[q] = xa[q]; im[q] = xi[q]; cm[q] = xc[q]; rm[q] = xr[q];
         } else if (q >= 1) {
-          am[q] = xa[q - 1]; dm[q] = xd[q - 1]; cm[q] = xc[q - 1]; rm[q] = xr[q - 1];
+          am[q] = xa[q - 1]; im[q] = xi[q - 1]; cm[q] = xc[q - 1]; rm[q] = xr[q - 1];
         } else {
-          am[q] = 0; dm[q] = 1; cm[q] = 0; rm[q] = 0;
+          am[q] = 0; im[q] = 1; cm[q] = 0; rm[q] = 0;
         }
         if (lane + s < 32) {
-          ap[q] = ya[q]; dp[q] = yd[q]; cp[q] = yc[q]; rp[q] = yr[q];
+          ap[q] = ya[q]; ip[q] = yi[q]; cp[q] = yc[q]; rp[q] = yr[q];
         } else if (q + 1 < KPL) {
-          ap[q] = ya[q + 1]; dp[q] = yd[q + 1]; cp[q] = yc[q + 1]; rp[q] = yr[q + 1];
+          ap[q] = ya[q + 1]; ip[q] = yi[q + 1]; cp[q] = yc[q + 1]; rp[q] = yr[q + 1];
         } else {
-          ap[q] = 0; dp[q] = 1; cp[q] = 0; rp[q] = 0;
+          ap[q] = 0; ip[q] = 1; cp[q] = 0; rp[q] = 0;
         }
       }
     } else {
@@ -150,20 +155,20 @@ __device__ __forceinline__ void pcr_solve(T (&a)[KPL], T (&d)[KPL], T (&c)[KPL],
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         if (q - t >= 0) {
-          am[q] = a[q - t]; dm[q] = d[q - t]; cm[q] = c[q - t]; rm[q] = r[q - t];
+          am[q] = a[q - t]; im[q] = iv[q - t]; cm[q] = c[q - t]; rm[q] = r[q - t];
         } else {
-          am[q] = 0; dm[q] = 1; cm[q] = 0; rm[q] = 0;
+          am[q] = 0; im[q] = 1; cm[q] = 0; rm[q] = 0;
         }
         if (q + t < KPL) {
-          ap[q] = a[q + t]; dp[q] = d[q + t]; cp[q] = c[q + t]; rp[q] = r[q + t];
+          ap[q] = a[q + t]; ip[q] = iv[q + t]; cp[q] = c[q + t]; rp[q] = r[q + t];
         } else {
-          ap[q] = 0; dp[q] = 1; cp[q] = 0; rp[q] = 0;
+          ap[q] = 0; ip[q] = 1; cp[q] = 0; rp[q] = 0;
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
-      T al = -a[q] / dm[q], ga = -c[q] / dp[q];
+      T al = -a[q] * im[q], ga = -c[q] * ip[q];
       T nd = d[q] + al * cm[q] + ga * ap[q];
       T nr = r[q] + al * rm[q] + ga * rp[q];
       a[q] = al * am[q];
@@ -184,12 +189,12 @@ __device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, in
   for (int q = 0; q < KPL; ++q) {
     int k = lane + 32 * q;
     if (k < S) {
-      i64 o = (i64)k * L.nc;
+      i64 o = (i64)k * L.ld;
       T tau = L.tau[o + c];
       T dg = 2 * tau, rhs = L.b[o + c];
 #pragma unroll
       for (int sl = 0; sl < 3; ++sl) {
-        T al = L.alpha[((i64)sl * S + k) * L.nc + c];
+        T al = L.alpha[((i64)sl * S + k) * L.ld + c];
         dg += al;
         if (nb[sl] >= 0) rhs += al * L.x[o + nb[sl]];
       }
@@ -205,7 +210,7 @@ __device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, in
 #pragma unroll
   for (int q = 0; q < KPL; ++q) {
     int k = lane + 32 * q;
-    if (k < S) L.x[(i64)k * L.nc + c] = r[q] / d[q];
+    if (k < S) L.x[(i64)k * L.ld + c] = mg_div(r[q], d[q]);
   }
 }
 
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T
   T* sd = reinterpret_cast<T*>(smem_raw);  // [S][P] diagonal
   T* sr = sd + S * P;                      // [S][P] right-hand side, then solution
   T* st = sr + S * P;                      // [S][P] tau
-  const int sq = L.m * L.m, nc = (int)L.nc;
+  const int sq = L.m * L.m, ld = (int)L.ld;
   const int j = threadIdx.x % kTileCells, row0 = threadIdx.x / kTileCells;
   const int rows = blockDim.x / kTileCells;
   const int cell = blockIdx.x * kTileCells + j;
@@ -243,13 +248,13 @@ __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T
   for (int k = row0; k < S; k += rows) {
     T dg = 1, rhs = 0, tau = 0;
     if (live) {
-      const int o = k * nc;
+      const int o = k * ld;
       tau = L.tau[o + c];
       dg = 2 * tau;
       rhs = L.b[o + c];
 #pragma unroll
       for (int sl = 0; sl < 3; ++sl) {
-        T al = L.alpha[(sl * S + k) * nc + c];
+        T al = L.alpha[(sl * S + k) * ld + c];
         dg += al;
         if (nb[sl] >= 0) rhs += al * L.x[o + (int)nb[sl]];
       }
@@ -279,12 +284,12 @@ __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
       int k = lane + 32 * q;
-      if (k < S) sr[k * P + col] = r[q] / d[q];
+      if (k < S) sr[k * P + col] = mg_div(r[q], d[q]);
     }
   }
   __syncthreads();
   if (live)
-    for (int k = row0; k < S; k += rows) L.x[k * nc + c] = sr[k * P + j];
+    for (int k = row0; k < S; k += rows) L.x[k * ld + c] = sr[k * P + j];
 }
 
 template <typename T>
@@ -295,7 +300,7 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
   if (L.tau) {
     int kpl = pcr_kpl(S);
     const size_t tile = 3 * (size_t)S * (kTileCells + 1) * sizeof(T);
-    if (kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.nc < (1ll << 31)) {
+    if (kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.ld < (1ll << 31)) {
       int blocks = (int)((sq + kTileCells - 1) / kTileCells);
       if (kpl == 1)
         launch(k_line_pcr_tile_kernel<T, 1>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
@@ -326,7 +331,7 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
 template <typename T>
 __global__ void k_residual_kernel(int S, LevelView<T> L) {
   SLICE_LOOP(k, S, c, L.nc) {
-    i64 i = (i64)k * L.nc + c;
+    i64 i = (i64)k * L.ld + c;
     L.r[i] = L.b[i] - level_apply(S, L, k, c);
   }
 }
@@ -341,10 +346,10 @@ void k_mg_residual(int S, const LevelView<T>& L, Stream st) {
 template <typename T>
 __global__ void k_restrict_kernel(int S, LevelView<T> f, LevelView<T> c) {
   SLICE_LOOP(k, S, C, c.nc) {
-    i64 i = (i64)k * c.nc + C;
+    i64 i = (i64)k * c.ld + C;
     i64 ch[4];
     children(c.m, decode(c.m, C), ch);
-    const T* rf = f.r + (i64)k * f.nc;
+    const T* rf = f.r + (i64)k * f.ld;
     c.b[i] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
   }
 }
@@ -356,7 +361,7 @@ void k_mg_restrict(int S, const LevelView<T>& fine, const LevelView<T>& coarse, 
 
 template <typename T>
 __global__ void k_prolong_kernel(int S, LevelView<T> c, LevelView<T> f) {
-  SLICE_LOOP(k, S, cf, f.nc) f.x[(i64)k * f.nc + cf] += c.x[(i64)k * c.nc + parent_of(f.m, cf)];
+  SLICE_LOOP(k, S, cf, f.nc) f.x[(i64)k * f.ld + cf] += c.x[(i64)k * c.ld + parent_of(f.m, cf)];
 }
 
 template <typename T>
@@ -365,48 +370,75 @@ void k_mg_prolong(int S, const LevelView<T>& coarse, const LevelView<T>& fine, S
 }
 
 // ------------------------------------------------------------------ coarsest grid
+// Walks the (slice, cell) pairs k nc + c of S nc cells in steps of blockDim.x
+// with one division per thread and level: (k, c) advance by (dk, dc).
+struct SliceWalk {
+  int k, c, dk, dc, nc;
+  __device__ SliceWalk(int nc_) : nc(nc_) {
+    k = threadIdx.x / nc;
+    c = threadIdx.x - k * nc;
+    dk = blockDim.x / nc;
+    dc = blockDim.x - dk * nc;
+  }
+  __device__ void next() {
+    k += dk;
+    c += dc;
+    if (c >= nc) {
+      c -= nc;
+      ++k;
+    }
+  }
+};
+
+// Threads of the one-CTA Schur kernels: 512 where a PCR lane's KPL systems in T
+// would not fit the 64 registers a 1024-thread CTA leaves each thread.
+template <typename T, int KPL>
+constexpr int sch_lower_threads() {
+  return sizeof(T) * KPL >= 16 ? 512 : 1024;
+}
+
 // One CTA: x = 0, `sweeps` red-black sweeps; for the space-time operator also
 // the correction on the single aggregate of all cells (the Galerkin operator
 // on the constant-per-slice space is the time-tridiagonal tau_G (2 d^k - d^{k-1} - d^{k+1}),
-// tau_G = sum of tau over the cells), followed by `sweeps` more sweeps.
+// tau_G = sum of tau over the cells), followed by `sweeps` more sweeps.  A
+// space-time level of side 1 is solved exactly instead.
 // KPL > 0: time lines and the aggregate system by warp PCR; KPL = 0: Thomas per thread.
 template <typename T, int KPL>
 __device__ void coarse_body(int S, const LevelView<T>& L, int sweeps, T* lc, T* lr, T* agg) {
-  i64 sq = (i64)L.m * L.m;
-  i64 tot = (i64)S * L.nc;
+  if (L.tau && L.m == 1) {
+    if (threadIdx.x == 0) coarse_exact_side1(S, L, agg);
+    __syncthreads();
+    return;
+  }
+  const int sq = L.m * L.m, nc = (int)L.nc;
+  const i64 ld = L.ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (i64 i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] = 0;
+  for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] = 0;
   __syncthreads();
   int passes = L.tau ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
     for (int it = 0; it < sweeps; ++it) {
       for (int color = 0; color < 2; ++color) {
         if (L.tau && KPL > 0) {
-          for (i64 w = warp; w < sq; w += nwarp) line_pcr<T, (KPL > 0 ? KPL : 1)>(S, L, (i64)color * sq + w, lane);
+          for (int w = warp; w < sq; w += nwarp) line_pcr<T, (KPL > 0 ? KPL : 1)>(S, L, (i64)color * sq + w, lane);
         } else if (L.tau) {
-          for (i64 i = threadIdx.x; i < sq; i += blockDim.x) line_gs(S, L, (i64)color * sq + i, lc, lr);
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) line_gs(S, L, (i64)color * sq + i, lc, lr);
         } else {
-          for (i64 i = threadIdx.x; i < (i64)S * sq; i += blockDim.x) {
-            int k = (int)(i / sq);
-            point_gs(S, L, k, (i64)color * sq + (i - (i64)k * sq));
-          }
+          for (SliceWalk w(sq); w.k < S; w.next()) point_gs(S, L, w.k, (i64)color * sq + w.c);
         }
         __syncthreads();
       }
     }
     if (!L.tau || pass == passes - 1) break;
     // aggregate correction
-    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) {
-      int k = (int)(i / L.nc);
-      L.r[i] = L.b[i] - level_apply(S, L, k, i - (i64)k * L.nc);
-    }
+    for (SliceWalk w(nc); w.k < S; w.next()) L.r[w.k * ld + w.c] = L.b[w.k * ld + w.c] - level_apply(S, L, w.k, w.c);
     __syncthreads();
     // agg[0..S): rhs, agg[S..2S): tau_G, agg[2S..3S): cp, agg[3S..4S): solution
     for (int k = threadIdx.x; k < S; k += blockDim.x) {
       T rsum = 0, tsum = 0;
-      for (i64 c = 0; c < L.nc; ++c) {
-        rsum += L.r[(i64)k * L.nc + c];
-        tsum += L.tau[(i64)k * L.nc + c];
+      for (int c = 0; c < nc; ++c) {
+        rsum += L.r[k * ld + c];
+        tsum += L.tau[k * ld + c];
       }
       agg[k] = rsum;
       agg[S + k] = tsum;
@@ -433,7 +465,7 @@ __device__ void coarse_body(int S, const LevelView<T>& L, int sweeps, T* lc, T* 
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           int k = lane + 32 * q;
-          if (k < S) agg[3 * S + k] = r[q] / d[q];
+          if (k < S) agg[3 * S + k] = mg_div(r[q], d[q]);
         }
       }
     } else if (threadIdx.x == 0) {
@@ -455,13 +487,14 @@ __device__ void coarse_body(int S, const LevelView<T>& L, int sweeps, T* lc, T* 
       }
     }
     __syncthreads();
-    for (i64 i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] += agg[3 * S + (int)(i / L.nc)];
+    for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] += agg[3 * S + w.k];
     __syncthreads();
   }
 }
 
 template <typename T, int KPL>
-__global__ void __launch_bounds__(1024) k_coarse_kernel(int S, LevelView<T> L, int sweeps, T* lc, T* lr, T* agg) {
+__global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_coarse_kernel(int S, LevelView<T> L, int sweeps,
+                                                                                T* lc, T* lr, T* agg) {
   coarse_body<T, KPL>(S, L, sweeps, lc, lr, agg);
 }
 
@@ -469,13 +502,13 @@ template <typename T>
 void k_mg_coarse_solve(int S, const LevelView<T>& L, int sweeps, T* line_c, T* line_r, T* agg, Stream st) {
   int kpl = L.tau ? pcr_kpl(S) : 0;
   if (kpl == 1)
-    launch(k_coarse_kernel<T, 1>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+    launch(k_coarse_kernel<T, 1>, 1, sch_lower_threads<T, 1>(), 0, cs(st), S, L, sweeps, line_c, line_r, agg);
   else if (kpl == 2)
-    launch(k_coarse_kernel<T, 2>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+    launch(k_coarse_kernel<T, 2>, 1, sch_lower_threads<T, 2>(), 0, cs(st), S, L, sweeps, line_c, line_r, agg);
   else if (kpl == 4)
-    launch(k_coarse_kernel<T, 4>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+    launch(k_coarse_kernel<T, 4>, 1, sch_lower_threads<T, 4>(), 0, cs(st), S, L, sweeps, line_c, line_r, agg);
   else
-    launch(k_coarse_kernel<T, 0>, 1, 1024, 0, cs(st), S, L, sweeps, line_c, line_r, agg);
+    launch(k_coarse_kernel<T, 0>, 1, sch_lower_threads<T, 0>(), 0, cs(st), S, L, sweeps, line_c, line_r, agg);
 }
 
 // ------------------------------------------------------------------ fused lower levels
@@ -490,6 +523,10 @@ struct LevelSet {
   LevelView<T> L[16];
 };
 
+// Slice stride of a staged level: odd when S_view > 1, so that a warp reading
+// one cell's time line (lane = slice) touches 32 different banks.
+__host__ __device__ inline i64 staged_ld(i64 nc, int S_view) { return (S_view > 1 && (nc & 1) == 0) ? nc + 1 : nc; }
+
 // Carve shared-memory views of the fused levels (S_view slices each) and copy
 // coefficients (slice `slice0` onwards) and the first level's b into them.
 template <typename T>
@@ -500,9 +537,10 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
     for (int l = 0; l < g.n; ++l) {
       const LevelView<T>& G = g.L[l];
       LevelView<T>& V = s.L[l];
-      const i64 n1 = (i64)S_view * G.nc;
       V.m = G.m;
       V.nc = G.nc;
+      V.ld = staged_ld(G.nc, S_view);
+      const i64 n1 = (i64)S_view * V.ld;
       V.alpha = p;
       p += 3 * n1;
       V.tau = G.tau ? p : nullptr;
@@ -519,19 +557,21 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
   for (int l = 0; l < g.n; ++l) {
     const LevelView<T>& G = g.L[l];
     const LevelView<T>& V = s.L[l];
-    // per edge slot the S_view staged slices are one contiguous run of n1 values
-    const int nc = (int)G.nc, n1 = S_view * nc;
+    const int nc = (int)G.nc, gld = (int)G.ld, vld = (int)V.ld;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
-      const T* src = G.alpha + ((i64)sl * S + slice0) * nc;
-      T* dst = V.alpha + (i64)sl * n1;
-#pragma unroll 4
-      for (int i = threadIdx.x; i < n1; i += blockDim.x) dst[i] = src[i];
+      const T* src = G.alpha + ((i64)sl * S + slice0) * gld;
+      T* dst = V.alpha + sl * S_view * vld;
+      for (SliceWalk w(nc); w.k < S_view; w.next()) dst[w.k * vld + w.c] = src[w.k * gld + w.c];
     }
-    if (G.tau)
-      for (int i = threadIdx.x; i < n1; i += blockDim.x) V.tau[i] = G.tau[(i64)slice0 * nc + i];
-    if (l == 0)
-      for (int i = threadIdx.x; i < n1; i += blockDim.x) V.b[i] = G.b[(i64)slice0 * nc + i];
+    if (G.tau) {
+      const T* src = G.tau + (i64)slice0 * gld;
+      for (SliceWalk w(nc); w.k < S_view; w.next()) V.tau[w.k * vld + w.c] = src[w.k * gld + w.c];
+    }
+    if (l == 0) {
+      const T* src = G.b + (i64)slice0 * gld;
+      for (SliceWalk w(nc); w.k < S_view; w.next()) V.b[w.k * vld + w.c] = src[w.k * gld + w.c];
+    }
   }
   __syncthreads();
 }
@@ -539,12 +579,12 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
 template <typename T>
 size_t fused_smem_bytes(const LevelView<T>* lv, int nlev, int S_view, bool tc) {
   size_t cells = 0;
-  for (int l = 0; l < nlev; ++l) cells += (size_t)S_view * lv[l].nc;
+  for (int l = 0; l < nlev; ++l) cells += (size_t)S_view * (size_t)staged_ld(lv[l].nc, S_view);
   return sizeof(T) * cells * (tc ? 7 : 6) + (tc ? sizeof(T) * 4 * (size_t)S_view : 0);
 }
 
 // Slice Laplacians: one CTA per slice (blockIdx.x), point red-black GS, the
-// slice's levels in shared memory.
+// slice's levels in shared memory (S_view = 1: stride = cells).
 template <typename T>
 __global__ void __launch_bounds__(256) k_lap_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -554,20 +594,20 @@ __global__ void __launch_bounds__(256) k_lap_lower_kernel(int S, LevelSet<T> gls
   const int last = ls.n - 1;
   for (int l = 0; l <= last; ++l) {
     const LevelView<T>& L = ls.L[l];
-    const i64 sq = (i64)L.m * L.m;
-    for (i64 i = threadIdx.x; i < L.nc; i += blockDim.x) L.x[i] = 0;
+    const int sq = L.m * L.m, nc = (int)L.nc;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) L.x[i] = 0;
     __syncthreads();
     const int sweeps = (l == last) ? nuc : nu;
     for (int it = 0; it < sweeps; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (i64 i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)col * sq + i);
+        for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
         __syncthreads();
       }
     if (l == last) break;
-    for (i64 c = threadIdx.x; c < L.nc; c += blockDim.x) L.r[c] = L.b[c] - level_apply(1, L, 0, c);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) L.r[c] = L.b[c] - level_apply(1, L, 0, c);
     __syncthreads();
     const LevelView<T>& Lc = ls.L[l + 1];
-    for (i64 C = threadIdx.x; C < Lc.nc; C += blockDim.x) {
+    for (int C = threadIdx.x; C < (int)Lc.nc; C += blockDim.x) {
       i64 ch[4];
       children(Lc.m, decode(Lc.m, C), ch);
       Lc.b[C] = L.r[ch[0]] + L.r[ch[1]] + L.r[ch[2]] + L.r[ch[3]];
@@ -577,76 +617,50 @@ __global__ void __launch_bounds__(256) k_lap_lower_kernel(int S, LevelSet<T> gls
   for (int l = last - 1; l >= 0; --l) {
     const LevelView<T>& L = ls.L[l];
     const LevelView<T>& Lc = ls.L[l + 1];
-    const i64 sq = (i64)L.m * L.m;
-    for (i64 c = threadIdx.x; c < L.nc; c += blockDim.x) L.x[c] += Lc.x[parent_of(L.m, c)];
+    const int sq = L.m * L.m, nc = (int)L.nc;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) L.x[c] += Lc.x[parent_of(L.m, c)];
     __syncthreads();
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
-        for (i64 i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)col * sq + i);
+        for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
         __syncthreads();
       }
   }
   const LevelView<T>& G0 = gls.L[0];
-  for (i64 i = threadIdx.x; i < G0.nc; i += blockDim.x) G0.x[(i64)k * G0.nc + i] = ls.L[0].x[i];
+  for (int i = threadIdx.x; i < (int)G0.nc; i += blockDim.x) G0.x[(i64)k * G0.ld + i] = ls.L[0].x[i];
 }
-
-// Walks the flat index i = k nc + c over S nc cells in steps of blockDim.x
-// with one division per thread and level: (k, c) advance by (dk, dc).
-struct SliceWalk {
-  int k, c, dk, dc, nc;
-  __device__ SliceWalk(int nc_) : nc(nc_) {
-    k = threadIdx.x / nc;
-    c = threadIdx.x - k * nc;
-    dk = blockDim.x / nc;
-    dc = blockDim.x - dk * nc;
-  }
-  __device__ void next() {
-    k += dk;
-    c += dc;
-    if (c >= nc) {
-      c -= nc;
-      ++k;
-    }
-  }
-};
 
 // Space-time Schur operator: one CTA for all slices, time lines by warp PCR,
-// all fused levels in shared memory; the coarsest level adds the aggregate
-// correction of k_coarse_kernel.
-// Threads of the fused Schur kernel: 512 where a PCR lane's KPL systems in T
-// would not fit the 64 registers a 1024-thread CTA leaves each thread.
+// all fused levels in shared memory with odd slice strides; the coarsest level
+// as in k_coarse_kernel.
 template <typename T, int KPL>
-constexpr int sch_lower_threads() {
-  return sizeof(T) * KPL >= 16 ? 512 : 1024;
-}
-
-template <typename T, int KPL>
-__global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
+__global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu,
+                                                                                   int nuc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   __shared__ LevelSet<T> ls;
   stage_levels(gls, ls, reinterpret_cast<T*>(smem_raw), S, S, 0);
-  T* agg = ls.L[ls.n - 1].r + (i64)S * ls.L[ls.n - 1].nc;
+  T* agg = ls.L[ls.n - 1].r + (i64)S * ls.L[ls.n - 1].ld;
   const int last = ls.n - 1;
   for (int l = 0; l < last; ++l) {
     const LevelView<T>& L = ls.L[l];
-    const int sq = L.m * L.m, nc = (int)L.nc, tot = S * nc;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) L.x[i] = 0;
+    const int sq = L.m * L.m, nc = (int)L.nc, ld = (int)L.ld;
+    for (int i = threadIdx.x; i < S * ld; i += blockDim.x) L.x[i] = 0;
     __syncthreads();
     for (int it = 0; it < nu; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
+        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
         __syncthreads();
       }
-    for (SliceWalk w(nc); w.k < S; w.next()) L.r[w.k * nc + w.c] = L.b[w.k * nc + w.c] - level_apply(S, L, w.k, w.c);
+    for (SliceWalk w(nc); w.k < S; w.next()) L.r[w.k * ld + w.c] = L.b[w.k * ld + w.c] - level_apply(S, L, w.k, w.c);
     __syncthreads();
     const LevelView<T>& Lc = ls.L[l + 1];
-    const int ncc = (int)Lc.nc;
-    for (SliceWalk w(ncc); w.k < S; w.next()) {
+    const int ldc = (int)Lc.ld;
+    for (SliceWalk w((int)Lc.nc); w.k < S; w.next()) {
       i64 ch[4];
       children(Lc.m, decode(Lc.m, w.c), ch);
-      const T* rf = L.r + w.k * nc;
-      Lc.b[w.k * ncc + w.c] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
+      const T* rf = L.r + w.k * ld;
+      Lc.b[w.k * ldc + w.c] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
     }
     __syncthreads();
   }
@@ -655,17 +669,18 @@ __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kerne
   for (int l = last - 1; l >= 0; --l) {
     const LevelView<T>& L = ls.L[l];
     const LevelView<T>& Lc = ls.L[l + 1];
-    const int sq = L.m * L.m, nc = (int)L.nc, ncc = (int)Lc.nc;
-    for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * nc + w.c] += Lc.x[w.k * ncc + (int)parent_of(L.m, w.c)];
+    const int sq = L.m * L.m, nc = (int)L.nc, ld = (int)L.ld, ldc = (int)Lc.ld;
+    for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] += Lc.x[w.k * ldc + (int)parent_of(L.m, w.c)];
     __syncthreads();
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
-        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)col * sq + w, lane);
+        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
         __syncthreads();
       }
   }
   const LevelView<T>& G0 = gls.L[0];
-  for (i64 i = threadIdx.x; i < (i64)S * G0.nc; i += blockDim.x) G0.x[i] = ls.L[0].x[i];
+  const LevelView<T>& V0 = ls.L[0];
+  for (SliceWalk w((int)G0.nc); w.k < S; w.next()) G0.x[(i64)w.k * G0.ld + w.c] = V0.x[w.k * (int)V0.ld + w.c];
 }
 
 // Opt a kernel into more than 48 KB of dynamic shared memory (once per size).
@@ -696,11 +711,18 @@ void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int n
   for (int i = 0; i < nlev; ++i) ls.L[i] = levels[i];
   const size_t bytes = k_mg_fused_smem(S, levels, nlev);
   if (bytes > kFusedSmemLimit) throw Error(1, "fused multigrid levels exceed shared memory");
+  // algorithmic bytes: every fused level's coefficients, the first level's b in and x out
+  double moved = 0.0;
+  for (int i = 0; i < nlev; ++i) moved += (levels[i].tau ? 4.0 : 3.0) * (double)S * (double)levels[i].nc;
+  moved = (double)sizeof(T) * (moved + 2.0 * (double)S * (double)levels[0].nc);
   if (!levels[0].tau) {
+    prof::begin(prof::LAP_LOWER, st);
     set_smem(k_lap_lower_kernel<T>, bytes);
     launch(k_lap_lower_kernel<T>, S, 256, bytes, cs(st), S, ls, nu, nuc);
+    prof::end(prof::LAP_LOWER, st, moved);
     return;
   }
+  prof::begin(prof::SCH_LOWER, st);
   int kpl = pcr_kpl(S);
   if (kpl == 1) {
     set_smem(k_sch_lower_kernel<T, 1>, bytes);
@@ -714,6 +736,7 @@ void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int n
   } else {
     throw Error(1, "fused Schur levels need K <= 128");
   }
+  prof::end(prof::SCH_LOWER, st, moved);
 }
 
 // ------------------------------------------------------------------ conversions

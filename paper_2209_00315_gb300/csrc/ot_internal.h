@@ -53,6 +53,8 @@ enum Id {
   SCHUR,         // Schur operator (2 kernels)
   RESIDUAL,      // residual F
   BT,            // B^T P^T y
+  LAP_LOWER,     // fused small levels of a slice-Laplacian V-cycle (one launch)
+  SCH_LOWER,     // fused small levels of a space-time Schur V-cycle (one launch)
   COUNT
 };
 extern bool enabled;        // any group on
@@ -171,12 +173,17 @@ void k_absmax(const double* x, i64 n, double* out, double* partial, Stream st);
 void k_min(const double* x, i64 n, double* out, double* partial, Stream st);
 
 // ------------------------------------------------------------------ multigrid (T = float or double)
+// Level arrays are slice-major with slice stride ld: cell c of slice k is
+// element k*ld + c (alpha: (slot*S + k)*ld + c).  Device-memory levels have
+// ld == nc; shared-memory copies pad ld to an odd stride so that the 32 lanes
+// of a time line hit 32 different banks.
 template <typename T>
 struct LevelView {
   int m;        // grid side
   i64 nc;       // cells per slice
-  T* alpha;     // [3][S][nc]
-  T* tau;       // [S][nc] or nullptr
+  i64 ld;       // slice stride, >= nc
+  T* alpha;     // [3][S][ld]
+  T* tau;       // [S][ld] or nullptr
   T* x;
   T* b;
   T* r;

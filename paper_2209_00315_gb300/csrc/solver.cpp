@@ -24,6 +24,7 @@ void Hierarchy<T>::build(int m0, int S_, bool tc) {
     LevelView<T> L;
     L.m = m;
     L.nc = 2LL * m * m;
+    L.ld = L.nc;
     size_t v = sizeof(T) * (size_t)S * L.nc;
     L.alpha = (T*)dev::alloc(3 * v);
     L.tau = tc ? (T*)dev::alloc(v) : nullptr;

@@ -1,0 +1,52 @@
+"""Command-line solve of one synthetic transport problem.
+
+    python -m paper_2209_00315_gb300.solve --workload mix64 --precision mixed
+
+runs the interior-point method (Sec. 3) on the GPU for a named seeded
+workload of ``ot_inputs`` and prints one JSON line with the cost, the
+iteration counts and the wall time of each solve.  Workloads: gauss8
+(8x8, K=8), mix64 (64x64, K=32), mix128 (128x128, K=32), fd32 (32x32,
+K=16), stress256 (256x256, K=64).
+"""
+import argparse
+import json
+import time
+
+import torch
+
+from . import capi
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--workload", default="mix64")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--repeat", type=int, default=1)
+    p.add_argument("--tol", type=float, default=1e-6, help="duality-gap target")
+    p.add_argument("--verbose", action="store_true", help="print one line per barrier stage")
+    a = p.parse_args(argv)
+
+    from ot_inputs import config_densities
+
+    n, K, r0, r1 = config_densities(a.workload)
+    mesh = capi.Mesh(n)
+    r0d = torch.from_numpy(r0).cuda()
+    r1d = torch.from_numpy(r1).cuda()
+    opt = capi.default_options(precision=a.precision, verbose=int(a.verbose))
+    walls, res = [], None
+    for _ in range(a.repeat):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = capi.ot_ipm_solve(mesh, r0d, r1d, K, tol=a.tol, options=opt)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
+    st = res["stats"]
+    print(json.dumps({
+        "workload": a.workload, "n": n, "K": K, "precision": a.precision, "cost": res["cost"],
+        "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"], "inner_iters": st["inner_iters"],
+        "gap": st["gap"], "wall_s": walls, "kernel_launches": capi.ot_kernel_launches(),
+    }))
+
+
+if __name__ == "__main__":
+    main()
