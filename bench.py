@@ -47,6 +47,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solves")
+    p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched solve")
+    p.add_argument("--batched-streams", type=int, default=16)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
 
@@ -248,6 +250,35 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": t_b / max(t_n, 1),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
 
+    # 5. the batched workload: 64 independent problems of uneven size on concurrent streams
+    batched = None
+    if not args.no_batched:
+        from ot_inputs import batched_problem_specs
+
+        specs = batched_problem_specs(64)
+        bmeshes, items = {}, []
+        for n_, K_, a_, b_ in specs:
+            if n_ not in bmeshes:
+                bmeshes[n_] = capi.Mesh(n_)
+            items.append((bmeshes[n_], torch.from_numpy(a_).to(dev), torch.from_numpy(b_).to(dev), K_))
+        bopt = capi.default_options(precision=args.precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            bout = capi.ot_ipm_solve_batched(items, options=bopt, n_streams=args.batched_streams)
+        except capi.OTError as e:
+            bout = None
+            batched = {"error": str(e)}
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+    if not args.no_batched and bout is not None:
+        batched = {"workload": "64 problems, side in {16,24,32,48,64}, K in {8,16,24,32}, 1-4 Gaussians, "
+                               "floor 1e-4 (seeds 1000..1063)",
+                   "precision": args.precision, "n_streams": args.batched_streams, "seconds": tb,
+                   "problems_per_s": len(items) / tb,
+                   "newton_steps": sum(o["stats"]["newton_steps"] for o in bout),
+                   "unknowns": sum((K_ + 1) * 8 * n_ * n_ + K_ * 2 * n_ * n_ for n_, K_, _, _ in specs)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, desc = oracle_sample_seconds()
@@ -265,9 +296,11 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                    "unknowns": Np + Nr},
         "solves_per_s": world * args.steps / (total / 1e3),
+        "newton_solves_per_s": world * st["newton_steps"] / sec,
         "result": {"cost": res["cost"], "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"],
                    "inner_iters": st["inner_iters"], "final_residual": st["final_residual"], "gap": st["gap"]},
         "fp64": fp64,
+        "batched": batched,
         "speedup_mixed_vs_fp64": (fp64["value"] / sec) if fp64 else None,
         "e2e": e2e_obj,
         "gpu_launches": launches,

@@ -140,6 +140,24 @@ ot_status ot_ipm_solve(ot_mesh* mesh, const double* rho_in, const double* rho_f,
                        double tol, const ot_options* opt, int32_t warm_start, double* rho, double* phi,
                        double* s, double* cost, ot_stats* stats, void* cuda_stream);
 
+/* Batched interior-point solves of n_prob independent problems of uneven size
+ * (the paper's method applied to each; the batching itself has no counterpart
+ * in the paper).  Problem p is ot_ipm_solve(meshes[p], rho_in[p], rho_f[p],
+ * K[p], mu0, tol, opt, no warm start, rho[p], phi[p], s[p], cost + p,
+ * stats + p); all arrays follow opt->memspace, as in ot_ipm_solve.  The
+ * problems run concurrently on n_streams (1..64) non-blocking CUDA streams of
+ * the current device, each driven by its own host thread with its own
+ * workspaces (largest problems first); the call returns when all are done.
+ *   cost, stats, status  nullable arrays of n_prob; status[p] = problem p's code
+ * Returns OT_OK, or the code of the first failed problem (the others still run
+ * to completion).  Kernel timing (ot_kernel_timing_enable) does not see these
+ * solves; the launch counter does.  The caller's meshes must stay alive and
+ * must not be used concurrently by other calls. */
+ot_status ot_ipm_solve_batched(int32_t n_prob, ot_mesh* const* meshes, const int32_t* K, const double* const* rho_in,
+                               const double* const* rho_f, double mu0, double tol, const ot_options* opt,
+                               double* const* rho, double* const* phi, double* const* s, double* cost,
+                               ot_stats* stats, int32_t* status, int32_t n_streams);
+
 /* One Newton direction at (phi, rho, s) for barrier parameter mu: the solution
  * of the Jacobian system (Eq. newton-linsys) obtained from the projected
  * saddle system (Eq. newton-linsys-shift-reduced-projected) by FGMRES + BB,

@@ -13,6 +13,7 @@ Modules
   mesh       generic triangle meshes, the midpoint 4-split, TPFA geometry (Sec. 2.1)
   operators  sparse matrices of Sec. 2.1-3 and of the projected / BB systems (Sec. 4.3)
   ipm        residual F, Jacobian, exact Newton directions, the IPM loop, cost and dual value
+  adjoint    gradient of the cost with respect to rho_in, rho_f (transposed-Jacobian solve)
 
 Parity unpinned: nothing here fixes the number of Krylov or multigrid
 iterations of the accelerated path; those are compared only qualitatively

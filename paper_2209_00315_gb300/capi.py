@@ -26,7 +26,7 @@ OT_PREC_FP64, OT_PREC_MIXED = 0, 1
 OT_MAX_STAGES = 40
 
 EXPORTED = ["ot_default_options", "ot_mesh_create", "ot_mesh_destroy", "ot_mesh_info", "ot_ipm_solve",
-            "ot_newton_solve", "ot_cost_grad", "ot_last_error", "ot_residual", "ot_kkt_apply", "ot_schur_apply",
+            "ot_ipm_solve_batched", "ot_newton_solve", "ot_cost_grad", "ot_last_error", "ot_residual", "ot_kkt_apply", "ot_schur_apply",
             "ot_bb_apply", "ot_cost_dual", "ot_kernel_timing_enable", "ot_kernel_timing_count",
             "ot_kernel_timing_read", "ot_kernel_launches", "ot_kkt_apply_noalloc"]
 
@@ -91,6 +91,8 @@ def load():
         "ot_mesh_info": (_I, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P]),
         "ot_ipm_solve": (_I, [_P, _P, _P, _I, _D, _D, C.POINTER(ot_options), _I, _P, _P, _P, C.POINTER(_D),
                               C.POINTER(ot_stats), _P]),
+        "ot_ipm_solve_batched": (_I, [_I, _P, _P, _P, _P, _D, _D, C.POINTER(ot_options), _P, _P, _P, _P,
+                                      C.POINTER(ot_stats), _P, _I]),
         "ot_newton_solve": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, C.POINTER(ot_options), _P, _P, _P,
                                  C.POINTER(ot_stats), _P]),
         "ot_cost_grad": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, C.POINTER(ot_options), _P, _P, _P]),
@@ -160,6 +162,9 @@ class Mesh:
         nc, nf, ne = C.c_int64(), C.c_int64(), C.c_int64()
         _check(self._lib.ot_mesh_info(self._h, C.byref(nc), C.byref(nf), C.byref(ne), None))
         self.n_coarse, self.n_fine, self.n_edges_fine = nc.value, nf.value, ne.value
+        areas = torch.empty(self.n_coarse, dtype=torch.float64)
+        _check(self._lib.ot_mesh_info(self._h, None, None, None, C.c_void_p(areas.data_ptr())))
+        self.coarse_areas = areas  # |c'| (host)
 
     @property
     def handle(self):
@@ -215,6 +220,48 @@ def ot_ipm_solve(mesh: Mesh, rho_in, rho_f, K: int, mu0: float = 1.0, tol: float
                                C.byref(o), int(warm_start is not None), rho.data_ptr(), phi.data_ptr(),
                                s.data_ptr(), C.byref(cost), C.byref(st), _stream(stream) if on_dev else 0))
     return {"rho": rho, "phi": phi, "s": s, "cost": cost.value, "stats": st.as_dict()}
+
+
+def ot_ipm_solve_batched(problems, mu0: float = 1.0, tol: float = 1e-6, options=None, n_streams: int = 16):
+    """Independent solves run concurrently on n_streams CUDA streams.
+
+    problems: list of (mesh, rho_in, rho_f, K) with CUDA float64 densities.
+    Returns one dict per problem, like ot_ipm_solve, plus its status code;
+    raises on the first failed problem after all have run."""
+    o = options if options is not None else default_options()
+    o.memspace = OT_MEM_DEVICE
+    n = len(problems)
+    keep = []
+    meshes = (_P * n)(*[p[0].handle for p in problems])
+    Ks = (_I * n)(*[int(p[3]) for p in problems])
+    out = []
+    for mesh, r0, r1, K in problems:
+        if not (isinstance(r0, torch.Tensor) and r0.is_cuda and isinstance(r1, torch.Tensor) and r1.is_cuda):
+            raise ValueError("ot_ipm_solve_batched takes CUDA densities")
+        r0 = r0.to(torch.float64).contiguous()
+        r1 = r1.to(torch.float64).contiguous()
+        dev = r0.device
+        Np, Nr = (K + 1) * mesh.n_fine, K * mesh.n_coarse
+        res = {"rho": torch.empty(Nr, dtype=torch.float64, device=dev),
+               "phi": torch.empty(Np, dtype=torch.float64, device=dev),
+               "s": torch.empty(Nr, dtype=torch.float64, device=dev)}
+        keep.append((r0, r1))
+        out.append(res)
+    ptrs = lambda xs: (_P * n)(*[x.data_ptr() for x in xs])  # noqa: E731
+    r0p, r1p = ptrs([k[0] for k in keep]), ptrs([k[1] for k in keep])
+    rhop, phip, sp = ptrs([r["rho"] for r in out]), ptrs([r["phi"] for r in out]), ptrs([r["s"] for r in out])
+    cost = (_D * n)()
+    stats = (ot_stats * n)()
+    status = (_I * n)()
+    torch.cuda.synchronize()
+    code = load().ot_ipm_solve_batched(n, meshes, Ks, r0p, r1p, float(mu0), float(tol), C.byref(o), rhop, phip, sp,
+                                       cost, stats, status, int(n_streams))
+    for p, res in enumerate(out):
+        res["cost"] = cost[p]
+        res["stats"] = stats[p].as_dict()
+        res["status"] = status[p]
+    _check(code)
+    return out
 
 
 def ot_newton_solve(mesh: Mesh, K: int, mu: float, phi, rho, s, rho_in, rho_f, options=None, stream=None):

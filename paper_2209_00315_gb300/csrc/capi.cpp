@@ -1,10 +1,13 @@
 // capi.cpp -- the extern "C" entry points of include/ot.h.
 #include <math.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -211,18 +214,14 @@ ot_status ot_mesh_info(const ot_mesh* mesh, int64_t* n_coarse, int64_t* n_fine, 
   OT_CATCH
 }
 
-ot_status ot_ipm_solve(ot_mesh* mesh, const double* rho_in, const double* rho_f, int32_t K, double mu0, double tol,
-                       const ot_options* opt_in, int32_t warm_start, double* rho, double* phi, double* s,
-                       double* cost, ot_stats* stats, void* cuda_stream) {
-  OT_TRY
-  ot_options o = resolve(opt_in);
-  require(mesh != nullptr, "mesh is NULL");
+// One interior-point solve in the workspace W (sized for the mesh and K).
+static void solve_in(Workspace& W, const ot_mesh* mesh, const double* rho_in, const double* rho_f, double mu0,
+                     double tol, const ot_options& o, int32_t warm_start, double* rho, double* phi, double* s,
+                     double* cost, ot_stats* stats, Stream st) {
   require(mu0 > 0 && tol > 0, "mu0 and tol must be positive");
   require(rho && phi && s, "output arrays are NULL");
-  Stream st = cuda_stream;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   check_boundary_densities(mesh, rho_in, rho_f, o, st);
-  Workspace& W = workspace(mesh, K, o);
   copy_in(W.r0, rho_in, W.d.Nc, o, st);
   copy_in(W.r1, rho_f, W.d.Nc, o, st);
   if (warm_start) {
@@ -247,6 +246,86 @@ ot_status ot_ipm_solve(ot_mesh* mesh, const double* rho_in, const double* rho_f,
     stats->cost = W.host[0];
     stats->dual = W.host[1];
   }
+}
+
+ot_status ot_ipm_solve(ot_mesh* mesh, const double* rho_in, const double* rho_f, int32_t K, double mu0, double tol,
+                       const ot_options* opt_in, int32_t warm_start, double* rho, double* phi, double* s,
+                       double* cost, ot_stats* stats, void* cuda_stream) {
+  OT_TRY
+  ot_options o = resolve(opt_in);
+  require(mesh != nullptr, "mesh is NULL");
+  Workspace& W = workspace(mesh, K, o);
+  solve_in(W, mesh, rho_in, rho_f, mu0, tol, o, warm_start, rho, phi, s, cost, stats, cuda_stream);
+  return OT_OK;
+  OT_CATCH
+}
+
+ot_status ot_ipm_solve_batched(int32_t n_prob, ot_mesh* const* meshes, const int32_t* K, const double* const* rho_in,
+                               const double* const* rho_f, double mu0, double tol, const ot_options* opt_in,
+                               double* const* rho, double* const* phi, double* const* s, double* cost,
+                               ot_stats* stats, int32_t* status, int32_t n_streams) {
+  OT_TRY
+  ot_options o = resolve(opt_in);
+  require(n_prob >= 0, "n_prob must be >= 0");
+  require(n_streams >= 1 && n_streams <= 64, "n_streams must be in [1, 64]");
+  if (n_prob == 0) return OT_OK;
+  require(meshes && K && rho_in && rho_f && rho && phi && s, "NULL argument");
+  for (int p = 0; p < n_prob; ++p) {
+    require(meshes[p] != nullptr, "a mesh is NULL");
+    require(K[p] >= 1 && K[p] <= 4096, "K must be in [1, 4096]");
+  }
+  const int device = dev::current_device();
+  // largest problems first, so that the last ones to start are the short ones
+  std::vector<int> order(n_prob);
+  for (int p = 0; p < n_prob; ++p) order[p] = p;
+  auto work = [&](int p) { return (double)meshes[p]->n * meshes[p]->n * (K[p] + 1.0); };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  std::atomic<int> next{0};
+  std::vector<int> codes(n_prob, OT_OK);
+  std::vector<std::string> msgs(n_prob);
+  auto worker = [&]() {
+    ot::prof::suspended = true;
+    Stream stream = nullptr;
+    try {
+      dev::set_device(device);
+      stream = dev::stream_create();
+    } catch (const std::exception& e) {
+      for (int i; (i = next.fetch_add(1)) < n_prob;) codes[order[i]] = OT_ERR_CUDA, msgs[order[i]] = e.what();
+      return;
+    }
+    // this thread's workspaces, one per (side, K)
+    std::map<std::pair<int, int>, std::unique_ptr<Workspace>> mine;
+    for (int i; (i = next.fetch_add(1)) < n_prob;) {
+      const int p = order[i];
+      try {
+        auto key = std::make_pair(meshes[p]->n, (int)K[p]);
+        auto it = mine.find(key);
+        if (it == mine.end())
+          it = mine.emplace(key, std::unique_ptr<Workspace>(new Workspace(meshes[p]->n, K[p], o.precision, o))).first;
+        solve_in(*it->second, meshes[p], rho_in[p], rho_f[p], mu0, tol, o, 0, rho[p], phi[p], s[p],
+                 cost ? cost + p : nullptr, stats ? stats + p : nullptr, stream);
+      } catch (const ot::Error& e) {
+        codes[p] = e.code, msgs[p] = e.what();
+      } catch (const std::bad_alloc&) {
+        codes[p] = OT_ERR_OOM, msgs[p] = "host allocation failed";
+      } catch (const std::exception& e) {
+        codes[p] = OT_ERR_CUDA, msgs[p] = e.what();
+      }
+    }
+    dev::sync_quiet(stream);
+    mine.clear();
+    dev::stream_destroy(stream);
+  };
+  const int nt = std::min<int>(n_streams, n_prob);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  int first = -1;
+  for (int p = 0; p < n_prob; ++p) {
+    if (status) status[p] = codes[p];
+    if (codes[p] != OT_OK && first < 0) first = p;
+  }
+  if (first >= 0) throw Error(codes[first], "problem " + std::to_string(first) + ": " + msgs[first]);
   return OT_OK;
   OT_CATCH
 }
@@ -357,7 +436,8 @@ ot_status ot_kkt_apply(ot_mesh* mesh, int32_t K, const double* phi, const double
   require(mesh && phi && rho && s && rho_in && rho_f && x && y, "NULL argument");
   Stream st = cuda_stream;
   Workspace& W = op_workspace(mesh, K);
-  ot::k_kkt_apply(W.d, phi, rho, s, rho_in, rho_f, x, y, W.xmean, nullptr, st);
+  ot::k_kkt_coef(W.d, phi, rho, s, rho_in, rho_f, W.kcoef, st);
+  ot::k_kkt_apply(W.d, W.kcoef, x, y, W.xmean, nullptr, st);
   dev::sync(st);
   return OT_OK;
   OT_CATCH

@@ -27,7 +27,8 @@ static void cuda_check(cudaError_t e, const char* where) {
 namespace prof {
 bool enabled = false;
 unsigned mask = 0;
-long long n_launch = 0;
+std::atomic<long long> n_launch{0};
+thread_local bool suspended = false;
 int stride = 1;
 namespace {
 unsigned long long seen[COUNT] = {0};
@@ -57,14 +58,14 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 void begin(int id, Stream s) {
-  if (!enabled || !((mask >> id) & 1u)) return;
+  if (!enabled || suspended || !((mask >> id) & 1u)) return;
   if (++seen[id] % (unsigned long long)stride != 0) return;
   cudaEvent_t e = get_event();
   cudaEventRecord(e, cs(s));
   open[id] = e;
 }
 void end(int id, Stream s, double bytes) {
-  if (!enabled || !open[id]) return;
+  if (!enabled || suspended || !open[id]) return;
   cudaEvent_t e = get_event();
   cudaEventRecord(e, cs(s));
   pending.push_back({id, open[id], e, bytes});
@@ -132,7 +133,7 @@ void copy_d2d(void* dst, const void* src, size_t bytes, Stream s) {
 void zero(void* dst, size_t bytes, Stream s) { cuda_check(cudaMemsetAsync(dst, 0, bytes, cs(s)), "cudaMemsetAsync"); }
 void sync(Stream s) {
   cuda_check(cudaStreamSynchronize(cs(s)), "cudaStreamSynchronize");
-  if (prof::enabled) prof::harvest();
+  if (prof::enabled && !prof::suspended) prof::harvest();
 }
 void check(const char* where) { cuda_check(cudaGetLastError(), where); }
 bool is_device_pointer(const void* p) {
@@ -146,6 +147,23 @@ bool is_device_pointer(const void* p) {
 double now() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+int current_device() {
+  int d = 0;
+  cuda_check(cudaGetDevice(&d), "cudaGetDevice");
+  return d;
+}
+void set_device(int device) { cuda_check(cudaSetDevice(device), "cudaSetDevice"); }
+Stream stream_create() {
+  cudaStream_t s = nullptr;
+  cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+  return (Stream)s;
+}
+void sync_quiet(Stream s) { cudaStreamSynchronize(cs(s)); }
+void stream_destroy(Stream s) {
+  if (!s) return;
+  cudaStreamSynchronize(cs(s));
+  cudaStreamDestroy(cs(s));
 }
 }  // namespace dev
 
@@ -169,6 +187,25 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Sum of v over the block; result valid in thread 0.  smem: blockDim/32 doubles.
+// Two-element vector types for paired loads.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> {
+  typedef double2 type;
+};
+template <>
+struct Pair<float> {
+  typedef float2 type;
+};
+
+// Paired loads need every row start (base + v*ld) and w on a pair boundary.
+template <typename T>
+static bool pair_aligned(const T* V, i64 ld, const T* w) {
+  const uintptr_t a = (uintptr_t)V | (uintptr_t)w;
+  return (a % (2 * sizeof(T))) == 0 && (ld % 2) == 0;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* smem) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_sum(v);
@@ -199,14 +236,13 @@ template <typename T>
 __global__ void k_slice_sums_kernel(const T* x, i64 n, double scale, T* sums) {
   __shared__ double sm[32];
   const T* xs = x + (i64)blockIdx.x * n;
-  double a = 0.0;
-  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += (double)xs[i];
+  double a = strided_sum(xs, n);
   a = block_sum(a, sm);
   if (threadIdx.x == 0) sums[blockIdx.x] = (T)(scale * a);
 }
 
 void k_slice_sums(const double* x, int S, i64 n, double scale, double* sums, Stream s) {
-  launch(k_slice_sums_kernel<double>, S, 512, 0, cs(s), x, n, scale, sums);
+  launch(k_slice_sums_kernel<double>, S, 1024, 0, cs(s), x, n, scale, sums);
 }
 
 template <typename T>
@@ -226,7 +262,8 @@ void k_slice_shift(double* x, int S, i64 n, const double* sums, double scale, St
 // keeps 8 accumulators (high occupancy); w is re-read per group from L2.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mdot8_kernel(const T* __restrict__ V, i64 ld, int nv,
-                                                      const T* __restrict__ w, i64 n, double* partial) {
+                                                      const T* __restrict__ w, i64 n, bool pairs,
+                                                      double* partial) {
   __shared__ double sm[8][8];
   const int v0 = blockIdx.y * 8;
   const int cnt = min(8, nv - v0);
@@ -234,7 +271,27 @@ __global__ void __launch_bounds__(256) k_mdot8_kernel(const T* __restrict__ V, i
   T acc[8];
 #pragma unroll
   for (int v = 0; v < 8; ++v) acc[v] = 0;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+  // each block walks one contiguous chunk (few address-translation pages at a
+  // time), two elements per load
+  i64 done = 0;
+  if (pairs) {
+    using V2 = typename Pair<T>::type;
+    const i64 np = n / 2, per = (np + gridDim.x - 1) / gridDim.x;
+    const i64 p0 = blockIdx.x * per, p1 = min(np, p0 + per);
+    const V2* w2 = reinterpret_cast<const V2*>(w);
+#pragma unroll 2
+    for (i64 q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+      const V2 wv = w2[q];
+#pragma unroll
+      for (int v = 0; v < 8; ++v)
+        if (v < cnt) {
+          const V2 x = reinterpret_cast<const V2*>(Vg + (i64)v * ld)[q];
+          acc[v] += x.x * wv.x + x.y * wv.y;
+        }
+    }
+    done = 2 * np;
+  }
+  for (i64 i = done + blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     T wi = w[i];
 #pragma unroll
     for (int v = 0; v < 8; ++v)
@@ -263,7 +320,8 @@ void k_mdot(const double* V, i64 ld, int nv, const double* w, i64 n, double* out
   prof::begin(prof::MDOT, s);
   int groups = (nv + 7) / 8;
   int bx = mdot_xblocks(groups);
-  launch(k_mdot8_kernel<double>, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, partial);
+  launch(k_mdot8_kernel<double>, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, pair_aligned(V, ld, w),
+         partial);
   launch(k_finish_sum, nv, 256, 0, cs(s), partial, bx, nv + 1, nv, out);
   prof::end(prof::MDOT, s, 8.0 * (double)(nv + 1) * (double)n);
 }
@@ -272,14 +330,41 @@ void k_mdot(const double* V, i64 ld, int nv, const double* w, i64 n, double* out
 // norm of the new w into partial[block].
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_kernel(const T* __restrict__ V, i64 ld, int nv,
-                                                       const double* __restrict__ h, T* w, i64 n, bool norm,
-                                                       double* partial) {
+                                                       const double* __restrict__ h, T* w, i64 n, bool pairs,
+                                                       bool norm, double* partial) {
   __shared__ T hs[64];
   __shared__ double sm[32];
   for (int v = threadIdx.x; v < 64; v += blockDim.x) hs[v] = (v < nv) ? (T)h[v] : (T)0;
   __syncthreads();
   T acc = 0;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+  i64 done = 0;
+  if (pairs) {
+    using V2 = typename Pair<T>::type;
+    const i64 np = n / 2, per = (np + gridDim.x - 1) / gridDim.x;
+    const i64 p0 = blockIdx.x * per, p1 = min(np, p0 + per);
+    V2* w2 = reinterpret_cast<V2*>(w);
+    for (i64 q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+      V2 wv = w2[q];
+      int v = 0;
+      for (; v + 8 <= nv; v += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const V2 x = reinterpret_cast<const V2*>(V + (i64)(v + u) * ld)[q];
+          wv.x -= hs[v + u] * x.x;
+          wv.y -= hs[v + u] * x.y;
+        }
+      }
+      for (; v < nv; ++v) {
+        const V2 x = reinterpret_cast<const V2*>(V + (i64)v * ld)[q];
+        wv.x -= hs[v] * x.x;
+        wv.y -= hs[v] * x.y;
+      }
+      w2[q] = wv;
+      acc += wv.x * wv.x + wv.y * wv.y;
+    }
+    done = 2 * np;
+  }
+  for (i64 i = done + blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     T wi = w[i];
     int v = 0;
     for (; v + 8 <= nv; v += 8) {
@@ -301,8 +386,8 @@ void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 
   for (int done = 0; done < nv; done += 64) {
     int c = nv - done < 64 ? nv - done : 64;
     bool last = done + c >= nv;
-    launch(k_update_kernel<double>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n, norm && last,
-           partial);
+    launch(k_update_kernel<double>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n,
+           pair_aligned(V, ld, (const double*)w), norm && last, partial);
   }
   if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out + nv);
   prof::end(prof::MUPDATE, s, 8.0 * (double)(nv + 2) * (double)n);
@@ -448,7 +533,7 @@ void k_min(const double* x, i64 n, double* out, double* partial, Stream s) {
 namespace ot {
 // ---- FP32 vectors (the preconditioner's inner Krylov solve in mixed precision)
 void k_slice_sums(const float* x, int S, i64 n, double scale, float* sums, Stream s) {
-  launch(k_slice_sums_kernel<float>, S, 512, 0, cs(s), x, n, scale, sums);
+  launch(k_slice_sums_kernel<float>, S, 1024, 0, cs(s), x, n, scale, sums);
 }
 void k_slice_shift(float* x, int S, i64 n, const float* sums, double scale, Stream s) {
   i64 tot = (i64)S * n;
@@ -458,7 +543,8 @@ void k_mdot(const float* V, i64 ld, int nv, const float* w, i64 n, double* out, 
   prof::begin(prof::MDOT, s);
   int groups = (nv + 7) / 8;
   int bx = mdot_xblocks(groups);
-  launch(k_mdot8_kernel<float>, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, partial);
+  launch(k_mdot8_kernel<float>, dim3(bx, groups), 256, 0, cs(s), V, ld, nv, w, n, pair_aligned(V, ld, w),
+         partial);
   launch(k_finish_sum, nv, 256, 0, cs(s), partial, bx, nv + 1, nv, out);
   prof::end(prof::MDOT, s, 4.0 * (double)(nv + 1) * (double)n);
 }
@@ -469,7 +555,7 @@ void k_mupdate(const float* V, i64 ld, int nv, const double* h, float* w, i64 n,
     int c = nv - done < 64 ? nv - done : 64;
     bool last = done + c >= nv;
     launch(k_update_kernel<float>, kRedBlocks, 256, 0, cs(s), V + (i64)done * ld, ld, c, h + done, w, n,
-           norm && last, partial);
+           pair_aligned(V, ld, (const float*)w), norm && last, partial);
   }
   if (norm) launch(k_finish_sum, 1, 256, 0, cs(s), partial, kRedBlocks, 1, 1, out + nv);
   prof::end(prof::MUPDATE, s, 4.0 * (double)(nv + 2) * (double)n);

@@ -14,6 +14,7 @@
 // stencil.cuh.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <unordered_map>
 
 #include "launch.cuh"
@@ -95,6 +96,11 @@ __global__ void k_point_smooth_kernel(int S, LevelView<T> L, int color) {
   i64 sq = (i64)L.m * L.m;
   SLICE_LOOP(k, S, i, sq) point_gs(S, L, k, (i64)color * sq + i);
 }
+
+// Point sweep of one colour in a non-plain mode: neighbour values as
+// sweep_neighbour gives them (zero, or x plus the coarse correction).
+template <typename T, int MODE>
+__global__ void k_point_smooth_mode_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color);
 
 template <typename T>
 __global__ void k_line_smooth_kernel(int S, LevelView<T> L, int color, T* lc, T* lr) {
@@ -230,8 +236,20 @@ static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128
 // into a padded [K][9] shared tile, warp w solves column w by PCR, and the
 // solutions leave through the same tile.
 constexpr int kTileCells = 8;
-template <typename T, int KPL>
-__global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T> L, int color) {
+// Sweep modes of the large-level smoothers (see k_mg_smooth_mode).
+enum { kSweepPlain = 0, kSweepFromZero = 1, kSweepAfterProlong = 2 };
+
+// Value of the spatial neighbour o of slice k as the sweep sees it.
+template <typename T, int MODE>
+__device__ __forceinline__ T sweep_neighbour(const LevelView<T>& L, const LevelView<T>& Lc, int k, int o) {
+  if (MODE == kSweepFromZero) return (T)0;
+  T v = L.x[(i64)k * L.ld + o];
+  if (MODE == kSweepAfterProlong) v += Lc.x[(i64)k * Lc.ld + parent_of(L.m, o)];
+  return v;
+}
+
+template <typename T, int KPL, int MODE>
+__global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
   constexpr int P = kTileCells + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sd = reinterpret_cast<T*>(smem_raw);  // [S][P] diagonal
@@ -256,7 +274,7 @@ __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T
       for (int sl = 0; sl < 3; ++sl) {
         T al = L.alpha[(sl * S + k) * ld + c];
         dg += al;
-        if (nb[sl] >= 0) rhs += al * L.x[o + (int)nb[sl]];
+        if (MODE != kSweepFromZero && nb[sl] >= 0) rhs += al * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
       }
     }
     sd[k * P + j] = dg;
@@ -292,6 +310,20 @@ __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T
     for (int k = row0; k < S; k += rows) L.x[k * ld + c] = sr[k * P + j];
 }
 
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per size).
+template <typename Kern>
+static void set_smem(Kern k, size_t bytes) {
+  static std::unordered_map<const void*, size_t> granted;
+  static std::mutex guard;  // concurrent solves share this table
+  if (bytes <= 48 * 1024) return;
+  std::lock_guard<std::mutex> lock(guard);
+  size_t& g = granted[reinterpret_cast<const void*>(k)];
+  if (bytes <= g) return;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) throw Error(7, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  g = bytes;
+}
+
 template <typename T>
 void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, Stream st) {
   i64 sq = (i64)L.m * L.m;
@@ -303,11 +335,11 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
     if (kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.ld < (1ll << 31)) {
       int blocks = (int)((sq + kTileCells - 1) / kTileCells);
       if (kpl == 1)
-        launch(k_line_pcr_tile_kernel<T, 1>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
+        launch(k_line_pcr_tile_kernel<T, 1, kSweepPlain>, blocks, 32 * kTileCells, tile, cs(st), S, L, L, color);
       else if (kpl == 2)
-        launch(k_line_pcr_tile_kernel<T, 2>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
+        launch(k_line_pcr_tile_kernel<T, 2, kSweepPlain>, blocks, 32 * kTileCells, tile, cs(st), S, L, L, color);
       else
-        launch(k_line_pcr_tile_kernel<T, 4>, blocks, 32 * kTileCells, tile, cs(st), S, L, color);
+        launch(k_line_pcr_tile_kernel<T, 4, kSweepPlain>, blocks, 32 * kTileCells, tile, cs(st), S, L, L, color);
       prof::end(id, st, (double)sizeof(T) * 7.0 * (double)S * (double)sq);
       return;
     }
@@ -324,6 +356,75 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
     launch(k_point_smooth_kernel<T>, slice_grid(sq, S), kT, 0, cs(st), S, L, color);
   }
   // per updated cell: b, three coefficients, the neighbours' x, the new x (+ tau for lines)
+  prof::end(id, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)sq);
+}
+
+template <typename T, int MODE>
+__global__ void k_point_smooth_mode_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  const int sq = L.m * L.m;
+  SLICE_LOOP(k, S, i, sq) {
+    const int c = color * sq + (int)i;
+    i64 nb[3];
+    neighbours(L.m, decode(L.m, c), nb);
+    T num = L.b[(i64)k * L.ld + c], den = 0;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      T a = L.alpha[((i64)sl * S + k) * L.ld + c];
+      den += a;
+      if (MODE != kSweepFromZero && nb[sl] >= 0) num += a * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
+    }
+    L.x[(i64)k * L.ld + c] = mg_div(num, den);
+  }
+}
+
+template <typename T>
+void k_mg_smooth_mode(int S, const LevelView<T>& L, const LevelView<T>* coarse, int color, int mode, T* line_c,
+                      T* line_r, Stream st) {
+  if (mode == kSweepPlain) {
+    k_mg_smooth<T>(S, L, color, line_c, line_r, st);
+    return;
+  }
+  if (mode == kSweepAfterProlong && !coarse) throw Error(1, "sweep after prolongation needs the coarse level");
+  const LevelView<T> Lc = coarse ? *coarse : L;
+  const i64 sq = (i64)L.m * L.m;
+  const int id = L.tau ? prof::SCH_SMOOTH : prof::LAP_SMOOTH;
+  const int kpl = L.tau ? pcr_kpl(S) : 0;
+  const size_t tile = 3 * (size_t)S * (kTileCells + 1) * sizeof(T);
+  if (L.tau && !(kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.ld < (1ll << 31))) {
+    // no tiled kernel for this shape: make the mode explicit, then a plain sweep
+    if (mode == kSweepFromZero)
+      dev::zero(L.x, sizeof(T) * (size_t)S * L.ld, st);
+    else
+      k_mg_prolong<T>(S, Lc, L, st);
+    k_mg_smooth<T>(S, L, color, line_c, line_r, st);
+    return;
+  }
+  prof::begin(id, st);
+  if (L.tau) {
+    const int blocks = (int)((sq + kTileCells - 1) / kTileCells);
+    const int thr = 32 * kTileCells;
+#define OT_TILE(Q, M) launch(k_line_pcr_tile_kernel<T, Q, M>, blocks, thr, tile, cs(st), S, L, Lc, color)
+    if (mode == kSweepFromZero) {
+      if (kpl == 1)
+        OT_TILE(1, kSweepFromZero);
+      else if (kpl == 2)
+        OT_TILE(2, kSweepFromZero);
+      else
+        OT_TILE(4, kSweepFromZero);
+    } else {
+      if (kpl == 1)
+        OT_TILE(1, kSweepAfterProlong);
+      else if (kpl == 2)
+        OT_TILE(2, kSweepAfterProlong);
+      else
+        OT_TILE(4, kSweepAfterProlong);
+    }
+#undef OT_TILE
+  } else if (mode == kSweepFromZero) {
+    launch(k_point_smooth_mode_kernel<T, kSweepFromZero>, slice_grid(sq, S), kT, 0, cs(st), S, L, Lc, color);
+  } else {
+    launch(k_point_smooth_mode_kernel<T, kSweepAfterProlong>, slice_grid(sq, S), kT, 0, cs(st), S, L, Lc, color);
+  }
   prof::end(id, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)sq);
 }
 
@@ -357,6 +458,28 @@ __global__ void k_restrict_kernel(int S, LevelView<T> f, LevelView<T> c) {
 template <typename T>
 void k_mg_restrict(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st) {
   launch(k_restrict_kernel<T>, slice_grid(coarse.nc, S), kT, 0, cs(st), S, fine, coarse);
+}
+
+// b_coarse = J^T (b - M x) without storing the fine residual: each coarse cell
+// sums its four children's residuals (same sums, same order as residual + restrict).
+template <typename T>
+__global__ void k_restrict_residual_kernel(int S, LevelView<T> f, LevelView<T> c) {
+  SLICE_LOOP(k, S, C, c.nc) {
+    i64 ch[4];
+    children(c.m, decode(c.m, C), ch);
+    const T* bf = f.b + (i64)k * f.ld;
+    T acc = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc += bf[ch[a]] - level_apply(S, f, k, ch[a]);
+    c.b[(i64)k * c.ld + C] = acc;
+  }
+}
+
+template <typename T>
+void k_mg_restrict_residual(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st) {
+  prof::begin(prof::MG_TRANSFER, st);
+  launch(k_restrict_residual_kernel<T>, slice_grid(coarse.nc, S), kT, 0, cs(st), S, fine, coarse);
+  prof::end(prof::MG_TRANSFER, st, (double)sizeof(T) * (fine.tau ? 6.0 : 5.0) * (double)S * (double)fine.nc);
 }
 
 template <typename T>
@@ -585,8 +708,9 @@ size_t fused_smem_bytes(const LevelView<T>* lv, int nlev, int S_view, bool tc) {
 
 // Slice Laplacians: one CTA per slice (blockIdx.x), point red-black GS, the
 // slice's levels in shared memory (S_view = 1: stride = cells).
+constexpr int kLapLowerThreads = 1024;  // one cell per thread and colour phase on a side-32 level
 template <typename T>
-__global__ void __launch_bounds__(256) k_lap_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
+__global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k = blockIdx.x;
   __shared__ LevelSet<T> ls;
@@ -683,18 +807,6 @@ __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kerne
   for (SliceWalk w((int)G0.nc); w.k < S; w.next()) G0.x[(i64)w.k * G0.ld + w.c] = V0.x[w.k * (int)V0.ld + w.c];
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory (once per size).
-template <typename Kern>
-static void set_smem(Kern k, size_t bytes) {
-  static std::unordered_map<const void*, size_t> granted;
-  if (bytes <= 48 * 1024) return;
-  size_t& g = granted[reinterpret_cast<const void*>(k)];
-  if (bytes <= g) return;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) throw Error(7, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-  g = bytes;
-}
-
 template <typename T>
 size_t k_mg_fused_smem(int S, const LevelView<T>* levels, int nlev) {
   bool tc = levels[0].tau != nullptr;
@@ -718,7 +830,7 @@ void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int n
   if (!levels[0].tau) {
     prof::begin(prof::LAP_LOWER, st);
     set_smem(k_lap_lower_kernel<T>, bytes);
-    launch(k_lap_lower_kernel<T>, S, 256, bytes, cs(st), S, ls, nu, nuc);
+    launch(k_lap_lower_kernel<T>, S, kLapLowerThreads, bytes, cs(st), S, ls, nu, nuc);
     prof::end(prof::LAP_LOWER, st, moved);
     return;
   }
@@ -768,6 +880,8 @@ void k_mg_store(const T* x, double* dst, i64 n, Stream st) {
   template void k_mg_smooth<T>(int, const LevelView<T>&, int, T*, T*, Stream);                                 \
   template void k_mg_residual<T>(int, const LevelView<T>&, Stream);                                            \
   template void k_mg_restrict<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);                       \
+  template void k_mg_restrict_residual<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);              \
+  template void k_mg_smooth_mode<T>(int, const LevelView<T>&, const LevelView<T>*, int, int, T*, T*, Stream);  \
   template void k_mg_prolong<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);                        \
   template void k_mg_coarse_solve<T>(int, const LevelView<T>&, int, T*, T*, T*, Stream);                       \
   template void k_mg_lower_cycle<T>(int, const LevelView<T>*, int, int, int, T*, T*, T*, Stream);              \

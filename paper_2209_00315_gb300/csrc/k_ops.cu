@@ -54,8 +54,7 @@ template <typename T>
 __global__ void k_slice_mean_kernel(const T* x, i64 n, T* mean) {
   __shared__ double sm[32];
   const T* xs = x + (i64)blockIdx.x * n;
-  double a = 0.0;
-  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += (double)xs[i];
+  double a = strided_sum(xs, n);
   a = warp_sum2(a);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sm[w] = a;
@@ -83,8 +82,7 @@ __global__ void k_project_kernel(double* w, i64 n, double* wsum) {
   __shared__ double sm[32];
   __shared__ double mean;
   double* ws = w + (i64)blockIdx.x * n;
-  double a = 0.0;
-  for (i64 i = threadIdx.x; i < n; i += blockDim.x) a += ws[i];
+  double a = strided_sum(ws, n);
   a = warp_sum2(a);
   int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   if (lane == 0) sm[wp] = a;
@@ -99,16 +97,56 @@ __global__ void k_project_kernel(double* w, i64 n, double* wsum) {
   for (i64 i = threadIdx.x; i < n; i += blockDim.x) ws[i] -= mean;
 }
 
-void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
-                 const double* r1, const double* x, double* y, double* xmean, double* wsum, Stream st) {
+__global__ void k_kkt_coef_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
+                                  double* kc) {
+  SLICE_LOOP(jj, d.K + 1, c, d.N) {
+    double w[3], g[3];
+    kkt_edge_coef(d, phi, rho, r0, r1, jj, c, w, g);
+    double* o = kc + (i64)jj * 6 * d.N + c;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      o[(i64)sl * d.N] = w[sl];
+      o[(i64)(3 + sl) * d.N] = g[sl];
+    }
+  }
+}
+
+__global__ void k_kkt_sr_kernel(Dims d, const double* rho, const double* s, double* sr) {
+  GRID_LOOP(i, (i64)d.K * d.Nc) sr[i] = d.area_c * s[i] / rho[i];
+}
+
+void k_kkt_coef(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
+                const double* r1, double* kc, Stream st) {
+  launch(k_kkt_coef_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, kc);
+  launch(k_kkt_sr_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, rho, s, kc + (i64)(d.K + 1) * 6 * d.N);
+}
+
+__global__ void k_kkt_phi_cached_kernel(Dims d, const double* kc, const double* xp, const double* xr,
+                                        const double* xmean, bool with_a, double* y) {
+  SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi_cached(d, kc, xp, xr, xmean, with_a, jj, c);
+}
+
+__global__ void k_kkt_rho_cached_kernel(Dims d, const double* kc, const double* xp, const double* xr,
+                                        const double* xmean, double* w) {
+  const double* sr = kc + (i64)(d.K + 1) * 6 * d.N;
+  SLICE_LOOP(k0, d.K, C, d.Nc) {
+    const i64 idx = (i64)k0 * d.Nc + C;
+    w[idx] = apply_B_cached(d, kc, xp, k0, C) - sr[idx] * (xr[idx] - xmean[k0]);
+  }
+}
+
+void k_kkt_apply(const Dims& d, const double* kc, const double* x, double* y, double* xmean, double* wsum,
+                 Stream st) {
   i64 Np = (i64)(d.K + 1) * d.N;
   const double* xr = x + Np;
   prof::begin(prof::KKT, st);
-  launch(k_slice_mean_kernel<double>, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
-  launch(k_kkt_phi_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
-  launch(k_kkt_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
-  launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, wsum);
-  prof::end(prof::KKT, st, 8.0 * (3.0 * Np + 4.0 * d.K * d.Nc));
+  launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), xr, d.Nc, xmean);
+  launch(k_kkt_phi_cached_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, x, xr, (const double*)xmean, true,
+         y);
+  launch(k_kkt_rho_cached_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, kc, x, xr, (const double*)xmean, y + Np);
+  launch(k_project_kernel, d.K, 1024, 0, cs(st), y + Np, d.Nc, wsum);
+  // x, y on both blocks, the six edge coefficients per fine cell and |C| s/rho
+  prof::end(prof::KKT, st, 8.0 * (2.0 * Np + 2.0 * d.K * d.Nc + 6.0 * Np + d.K * d.Nc));
 }
 
 // ---- KKT operator with file-scope scratch (no allocation by the call).
@@ -137,19 +175,19 @@ void k_kkt_apply_static(const Dims& d, const double* phi, const double* rho, con
   double* xmean = kkt_static_scratch();
   i64 Np = (i64)(d.K + 1) * d.N;
   const double* xr = x + Np;
-  launch(k_slice_mean_kernel<double>, d.K, 512, 0, cs(st), xr, d.Nc, xmean);
+  launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), xr, d.Nc, xmean);
   launch(k_kkt_phi_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, rho, r0, r1, x, xr, xmean, true, y);
   launch(k_kkt_rho_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, x, xr, xmean, y + Np);
-  launch(k_project_kernel, d.K, 512, 0, cs(st), y + Np, d.Nc, (double*)nullptr);
+  launch(k_project_kernel, d.K, 1024, 0, cs(st), y + Np, d.Nc, (double*)nullptr);
 }
 
-void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_phi, double* yr_mean, Stream st) {
+void k_bt_apply(const Dims& d, const double* kc, const double* yr, double* out_phi, double* yr_mean, Stream st) {
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);
-  launch(k_slice_mean_kernel<double>, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
-  launch(k_kkt_phi_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, nullptr, nullptr, nullptr, nullptr, yr, yr_mean, false,
-                                                 out_phi);
-  prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc));
+  launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), yr, d.Nc, yr_mean);
+  launch(k_kkt_phi_cached_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, (const double*)nullptr, yr,
+         (const double*)yr_mean, false, out_phi);
+  prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc + 3.0 * Np));
 }
 
 // ------------------------------------------------------------------ Schur operator
@@ -391,7 +429,7 @@ void k_adjoint_rhs(const Dims& d, const double* phi, const double* rho, const do
   i64 Np = (i64)(d.K + 1) * d.N;
   launch(k_adj_rhs_phi, nblk(Np), kT, 0, cs(st), d, phi, rho, r0, r1, rhs);
   launch(k_adj_rhs_rho, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, phi, rhs + Np);
-  launch(k_project_kernel, d.K, 512, 0, cs(st), rhs + Np, d.Nc, gsum);
+  launch(k_project_kernel, d.K, 1024, 0, cs(st), rhs + Np, d.Nc, gsum);
 }
 
 // grad_in = dt/4 R_T (grad phi^1)^2 - lambda^T dF/drho_in, grad_f likewise with phi^{K+1}.
@@ -412,7 +450,7 @@ namespace ot {
 void k_bt_apply(const Dims& d, const float* phi, const float* yr, float* out_phi, float* yr_mean, Stream st) {
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);
-  launch(k_slice_mean_kernel<float>, d.K, 512, 0, cs(st), yr, d.Nc, yr_mean);
+  launch(k_slice_mean_kernel<float>, d.K, 1024, 0, cs(st), yr, d.Nc, yr_mean);
   launch(k_kkt_phi_kernel<float>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, (const float*)nullptr,
          (const float*)nullptr, (const float*)nullptr, (const float*)nullptr, yr, (const float*)yr_mean, false, out_phi);
   prof::end(prof::BT, st, 4.0 * (2.0 * Np + (double)d.K * d.Nc));

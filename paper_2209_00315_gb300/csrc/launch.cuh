@@ -22,6 +22,25 @@ inline dim3 slice_grid(long long n, int S, int threads = 256) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; \
          c < (n); c += (long long)gridDim.x * blockDim.x)
 
+// This thread's share of sum_i xs[i] over a strided walk of n values, in
+// double, with four independent loads in flight per iteration: a block
+// reduces one slice of tens of thousands of values, and a single dependent
+// accumulator would wait for each load in turn.
+template <typename T>
+__device__ __forceinline__ double strided_sum(const T* xs, long long n) {
+  const long long b = blockDim.x;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  long long i = threadIdx.x;
+  for (; i + 3 * b < n; i += 4 * b) {
+    a0 += (double)xs[i];
+    a1 += (double)xs[i + b];
+    a2 += (double)xs[i + 2 * b];
+    a3 += (double)xs[i + 3 * b];
+  }
+  for (; i < n; i += b) a0 += (double)xs[i];
+  return (a0 + a1) + (a2 + a3);
+}
+
 template <typename... KArgs, typename... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
   ++prof::n_launch;

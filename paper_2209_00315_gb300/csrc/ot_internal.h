@@ -7,6 +7,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <stdexcept>
 #include <string>
 
@@ -35,6 +36,11 @@ void sync(Stream s);
 void check(const char* where);                   // throws Error(OT_ERR_CUDA) on a pending error
 bool is_device_pointer(const void* p);
 double now();                                    // seconds, host clock
+int current_device();
+void set_device(int device);
+Stream stream_create();                          // non-blocking stream
+void stream_destroy(Stream s);                   // after synchronising it
+void sync_quiet(Stream s);                       // synchronise, ignoring errors
 }  // namespace dev
 
 // ------------------------------------------------------------------ kernel timing
@@ -59,7 +65,10 @@ enum Id {
 };
 extern bool enabled;        // any group on
 extern unsigned mask;       // bit i: group i on
-extern long long n_launch;  // kernel launches since load (every launch, timing on or off)
+extern std::atomic<long long> n_launch;  // kernel launches since load (every launch, timing on or off)
+// Timing is per process and single-stream: threads that drive concurrent
+// solves (ot_ipm_solve_batched) set `suspended` and are never timed.
+extern thread_local bool suspended;
 extern int stride;          // time one launch in `stride` of each enabled group
 void begin(int id, Stream s);
 void end(int id, Stream s, double bytes);
@@ -108,10 +117,14 @@ void k_scale(const float* x, double a, float* y, i64 n, Stream s);
 // ------------------------------------------------------------------ operators (FP64)
 void k_residual(const Dims& d, double mu, const double* phi, const double* rho, const double* s,
                 const double* r0, const double* r1, double* Fphi, double* Frho, double* Fs, Stream st);
-// xmean[K] = slice means of x_rho; y = projected KKT operator applied to x.
+// Edge coefficients of the KKT operator at (phi, rho, s): kc holds
+// kkt_coef_count(d) doubles (layout in stencil.cuh).
+void k_kkt_coef(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
+                const double* r1, double* kc, Stream st);
+// xmean[K] = slice means of x_rho; y = projected KKT operator (coefficients kc) applied to x.
 // wsum (nullable, K): slice sums of B x_phi - C P^T x_rho before the projection.
-void k_kkt_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
-                 const double* r1, const double* x, double* y, double* xmean, double* wsum, Stream st);
+void k_kkt_apply(const Dims& d, const double* kc, const double* x, double* y, double* xmean, double* wsum,
+                 Stream st);
 // The same operator with its slice-mean scratch in a file-scope device array
 // (no allocation); K <= kStaticKktMaxK.  The first call on a device resolves
 // the array's address (cudaGetSymbolAddress) with that device current.
@@ -119,8 +132,8 @@ constexpr int kStaticKktMaxK = 4096;
 constexpr int kStaticKktMaxDevices = 64;
 void k_kkt_apply_static(const Dims& d, const double* phi, const double* rho, const double* s, const double* r0,
                         const double* r1, const double* x, double* y, Stream st);
-// y_phi = B^T P^T y_rho (phi rows only, no A term); yr_mean: scratch K.
-void k_bt_apply(const Dims& d, const double* phi, const double* yr, double* out_phi, double* yr_mean, Stream st);
+// y_phi = B^T P^T y_rho (phi rows only, no A term) from the KKT coefficients kc; yr_mean: scratch K.
+void k_bt_apply(const Dims& d, const double* kc, const double* yr, double* out_phi, double* yr_mean, Stream st);
 // Schur operator of Eq. (pseudoschur-bis); u: scratch (K+1) N.
 void k_schur_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* z,
                    double* out, double* u, Stream st);
@@ -198,8 +211,19 @@ template <typename T>
 void k_mg_restrict_coef(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st);
 template <typename T>
 void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, Stream st);
+// A sweep of one colour in a mode: 0 plain; 1 the first sweep from x = 0
+// (neighbour values taken as zero, x need not be initialised); 2 the first
+// sweep after a coarse correction (neighbour values x + J x_coarse; the
+// correction itself is never stored, because the next sweep of the other
+// colour overwrites those cells without reading them).
+template <typename T>
+void k_mg_smooth_mode(int S, const LevelView<T>& L, const LevelView<T>* coarse, int color, int mode, T* line_c,
+                      T* line_r, Stream st);
 template <typename T>
 void k_mg_residual(int S, const LevelView<T>& L, Stream st);
+// b_coarse = J^T (b - M x) in one pass (no fine residual stored)
+template <typename T>
+void k_mg_restrict_residual(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st);
 template <typename T>
 void k_mg_restrict(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st);
 template <typename T>

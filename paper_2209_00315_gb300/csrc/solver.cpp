@@ -133,6 +133,7 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
     xmean = dalloc(K + 2);
     mass = dalloc(K + 2);
     scal = dalloc(64 + 2 * (K + 2));
+    kcoef = dalloc(kkt_coef_count(d));
     int mm = std::max(opt.fgmres_restart, opt.schur_max_iter) + 2;
     partial = dalloc((i64)k_reduce_scratch(mm < 64 ? 64 : mm));
     u = dalloc(Np);
@@ -194,10 +195,10 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
 
 Workspace::~Workspace() {
   double* bufs[] = {phi, rho, s, r0, r1, Fphi, Frho, Fs, rhs, sol, ytmp, hvec, ds, gsum, wsum, cshift, xmean,
-                    mass, scal, partial, u, bphi, srhs, zeta};
+                    mass, scal, partial, u, bphi, srhs, zeta, kcoef};
   for (double* b : bufs) dev::release(b);
   phi = rho = s = r0 = r1 = Fphi = Frho = Fs = rhs = sol = ytmp = hvec = ds = nullptr;
-  gsum = wsum = cshift = xmean = mass = scal = partial = u = bphi = srhs = zeta = nullptr;
+  gsum = wsum = cshift = xmean = mass = scal = partial = u = bphi = srhs = zeta = kcoef = nullptr;
   outer.release();
   inner.release();
   innerf.release();
@@ -223,16 +224,28 @@ static void vcycle(Hierarchy<T>& H, size_t l, int nu, int nuc, Stream st) {
     k_mg_coarse_solve<T>(H.S, L, nuc, H.line_c, H.line_r, H.agg, st);
     return;
   }
-  dev::zero(L.x, sizeof(T) * (size_t)H.S * L.nc, st);
-  for (int i = 0; i < nu; ++i) {
+  LevelView<T>& Lc = H.lv[l + 1];
+  if (nu == 0) {
+    dev::zero(L.x, sizeof(T) * (size_t)H.S * L.nc, st);
+    k_mg_residual<T>(H.S, L, st);
+    k_mg_restrict<T>(H.S, L, Lc, st);
+    vcycle(H, l + 1, nu, nuc, st);
+    k_mg_prolong<T>(H.S, Lc, L, st);
+    return;
+  }
+  // pre-smoothing from x = 0: the first sweep reads no neighbour value
+  k_mg_smooth_mode<T>(H.S, L, nullptr, 0, 1, H.line_c, H.line_r, st);
+  k_mg_smooth<T>(H.S, L, 1, H.line_c, H.line_r, st);
+  for (int i = 1; i < nu; ++i) {
     k_mg_smooth<T>(H.S, L, 0, H.line_c, H.line_r, st);
     k_mg_smooth<T>(H.S, L, 1, H.line_c, H.line_r, st);
   }
-  k_mg_residual<T>(H.S, L, st);
-  k_mg_restrict<T>(H.S, L, H.lv[l + 1], st);
+  k_mg_restrict_residual<T>(H.S, L, Lc, st);
   vcycle(H, l + 1, nu, nuc, st);
-  k_mg_prolong<T>(H.S, H.lv[l + 1], L, st);
-  for (int i = 0; i < nu; ++i) {
+  // post-smoothing: the first sweep adds the coarse correction to the neighbours it reads
+  k_mg_smooth_mode<T>(H.S, L, &Lc, 1, 2, H.line_c, H.line_r, st);
+  k_mg_smooth<T>(H.S, L, 0, H.line_c, H.line_r, st);
+  for (int i = 1; i < nu; ++i) {
     k_mg_smooth<T>(H.S, L, 1, H.line_c, H.line_r, st);
     k_mg_smooth<T>(H.S, L, 0, H.line_c, H.line_r, st);
   }
@@ -292,6 +305,7 @@ static void refresh_t(Workspace& W, Hierarchy<T>& lap, Hierarchy<T>& sch, Stream
 }
 
 void refresh_coefficients(Workspace& W, Stream st) {
+  k_kkt_coef(W.d, W.phi, W.rho, W.s, W.r0, W.r1, W.kcoef, st);
   if (W.precision == OT_PREC_MIXED) {
     refresh_t(W, W.lapf, W.schf, st);
     k_convert(W.phi, W.phif, W.Np, 1.0, st);
@@ -414,7 +428,10 @@ static void bb_apply_t(Workspace& W, const ot_options& opt, Hierarchy<T>& lap, H
   k_atilde_minv(d, B.rho, B.zeta, yt, st);
   if constexpr (!f64) k_convert(yt, y, W.Nr, 1.0, st);
   // b = c - B^T P^T y, kept in the range of A (zero slice sums)
-  k_bt_apply(d, B.phi, yt, B.bphi, B.mean, st);
+  if constexpr (f64)
+    k_bt_apply(d, W.kcoef, yt, B.bphi, B.mean, st);
+  else
+    k_bt_apply(d, B.phi, yt, B.bphi, B.mean, st);
   if constexpr (f64)
     k_axpby(1.0, c, -1.0, B.bphi, W.Np, st);
   else
@@ -442,7 +459,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   k_scale(b, 1.0 / beta, K.V, n, st);
   OpFn<double> prec = [&](const double* in, double* out) { bb_apply(W, opt, in, out, st); };
   OpFn<double> op = [&](const double* in, double* out) {
-    k_kkt_apply(W.d, W.phi, W.rho, W.s, W.r0, W.r1, in, out, W.xmean, nullptr, st);
+    k_kkt_apply(W.d, W.kcoef, in, out, W.xmean, nullptr, st);
   };
   int total = 0;
   double res = beta;
@@ -491,7 +508,7 @@ void recover_direction(Workspace& W, Stream st) {
   double* sm = W.scal + 64;
   k_slice_sums(drho, d.K, d.Nc, 1.0 / (double)d.Nc, sm, st);
   k_slice_shift(drho, d.K, d.Nc, sm, 1.0, st);
-  k_kkt_apply(d, W.phi, W.rho, W.s, W.r0, W.r1, W.sol, W.ytmp, W.xmean, W.wsum, st);
+  k_kkt_apply(d, W.kcoef, W.sol, W.ytmp, W.xmean, W.wsum, st);
   k_shift_constants(d, W.gsum, W.wsum, 1.0, W.cshift, st);
   k_slice_shift(dphi, d.K + 1, d.N, W.cshift, -1.0, st);
   k_slice_sums(dphi, 1, W.Np, 1.0 / (double)W.Np, sm, st);

@@ -68,6 +68,7 @@ struct Workspace {
   double *Fphi = nullptr, *Frho = nullptr, *Fs = nullptr;
   double *rhs = nullptr, *sol = nullptr, *hvec = nullptr, *ds = nullptr, *ytmp = nullptr;
   double *gsum = nullptr, *wsum = nullptr, *cshift = nullptr, *xmean = nullptr, *mass = nullptr;
+  double* kcoef = nullptr;    // KKT edge coefficients at the current state (kkt_coef_count doubles)
   double* scal = nullptr;     // 64 device scalars
   double* partial = nullptr;  // reduction scratch
   // BB
@@ -89,7 +90,8 @@ struct Workspace {
   ~Workspace();
 };
 
-// Level-0 coefficients of both hierarchies and their coarsenings from the current (rho, s).
+// KKT edge coefficients, level-0 coefficients of both hierarchies and their
+// coarsenings (and the FP32 state copies) from the current (phi, rho, s).
 void refresh_coefficients(Workspace& W, Stream st);
 // One BB preconditioner application (Sec. 4.3): out = P_BB^{-1} v, both of length ntot.
 void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st);

@@ -276,6 +276,90 @@ OT_HD T kkt_rho(const Dims& d, const T* phi, const T* rho, const T* s, const T* 
   return apply_B(d, phi, xp, k0, C) - (T)d.area_c * s[idx] / rho[idx] * xh;
 }
 
+// ----------------------------------------------------------------- KKT with edge coefficients
+// The KKT rows above spend most of their time on FP64 arithmetic that depends
+// only on (phi, rho): the edge weights of the A block and the potential
+// differences of the B block.  Computed once per Newton step into
+//   kc[(jj*6 + sl)*N + c]     = w = T_e (rho~_c + rho~_o)/2,
+//   kc[(jj*6 + 3 + sl)*N + c] = g = T_e (phi^jj_c - phi^jj_o)/2   (zero on boundary slots),
+//   kc[(K+1)*6*N + k0*N' + C] = |C| s/rho,
+// every later operator application is loads plus a few FMAs per row.
+OT_HD i64 kkt_coef_count(const Dims& d) { return (i64)(d.K + 1) * 6 * d.N + (i64)d.K * d.Nc; }
+
+OT_HD void kkt_edge_coef(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
+                         int jj, i64 c, double w[3], double g[3]) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
+  const double* ph = phi + (i64)jj * d.N;
+  const double rc = rho_bar(d, rho, r0, r1, jj, parent(d.m, q));
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) {
+      w[sl] = 0.0;
+      g[sl] = 0.0;
+      continue;
+    }
+    const double t = trans(sl);
+    w[sl] = t * (0.5 * (rc + rho_bar(d, rho, r0, r1, jj, parent(d.m, nq[sl]))));
+    g[sl] = t * (0.5 * (ph[c] - ph[nb[sl]]));
+  }
+}
+
+// kkt_phi from the edge coefficients (with_a = false: the B^T P^T part only).
+OT_HD double kkt_phi_cached(const Dims& d, const double* kc, const double* xp, const double* xr,
+                            const double* xmean, bool with_a, int jj, i64 c) {
+  Cell q = decode(d.m, c);
+  i64 nb[3];
+  Cell nq[3];
+  neighbours(d.m, q, nb, nq);
+  i64 P = parent(d.m, q);
+  const double* xs = xp + (i64)jj * d.N;
+  const double* ym = (jj >= 1) ? xr + (i64)(jj - 1) * d.Nc : nullptr;
+  const double* yp = (jj <= d.K - 1) ? xr + (i64)jj * d.Nc : nullptr;
+  double mm = (jj >= 1) ? xmean[jj - 1] : 0.0, mp = (jj <= d.K - 1) ? xmean[jj] : 0.0;
+  double yma = ym ? ym[P] - mm : 0.0, ypa = yp ? yp[P] - mp : 0.0;
+  double acc = d.area_f * (yma - ypa) / d.dt;
+  double ybc = 0.5 * (yma + ypa);
+  double xc = with_a ? xs[c] : 0.0;
+  const double* kw = kc + (i64)jj * 6 * d.N + c;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (nb[sl] < 0) continue;
+    i64 Po = parent(d.m, nq[sl]);
+    double ybo = 0.5 * ((ym ? ym[Po] - mm : 0.0) + (yp ? yp[Po] - mp : 0.0));
+    acc += kw[(i64)(3 + sl) * d.N] * (ybc + ybo);
+    if (with_a) acc += kw[(i64)sl * d.N] * (xc - xs[nb[sl]]);
+  }
+  return acc;
+}
+
+// (B x)^k on coarse cell C from the edge coefficients: 1/4 T_e dphi dx = g dx / 2.
+OT_HD double apply_B_cached(const Dims& d, const double* kc, const double* x, int k0, i64 C) {
+  i64 ch[4];
+  children(d.n, decode(d.n, C), ch);
+  const double* x0 = x + (i64)k0 * d.N;
+  const double* x1 = x0 + d.N;
+  const double* g0 = kc + ((i64)k0 * 6 + 3) * d.N;
+  const double* g1 = kc + ((i64)(k0 + 1) * 6 + 3) * d.N;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    i64 c = ch[a];
+    i64 nb[3];
+    neighbours(d.m, decode(d.m, c), nb);
+    acc += d.area_f * (x1[c] - x0[c]) / d.dt;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      if (nb[sl] < 0) continue;
+      i64 o = nb[sl];
+      acc += 0.5 * (g0[(i64)sl * d.N + c] * (x0[c] - x0[o]) + g1[(i64)sl * d.N + c] * (x1[c] - x1[o]));
+    }
+  }
+  return acc;
+}
+
 // ----------------------------------------------------------------- BB pieces
 // u = M^{-1} B~ z on fine cell c, phi slice jj (paper j = jj+1), reading of Sec. 4.3.2:
 //   (z^j - z^{j-1})_Pc/dt + 1/(2|c|) sum_e T_e (phi^j_c - phi^j_o)(zbar^j_Pc - zbar^j_Po),

@@ -28,7 +28,7 @@ def lib_path():
 def test_header_declares_the_boundary():
     names = _declared()
     for must in ["ot_mesh_create", "ot_mesh_destroy", "ot_mesh_info", "ot_ipm_solve", "ot_newton_solve",
-                 "ot_cost_grad", "ot_last_error"]:
+                 "ot_cost_grad", "ot_last_error", "ot_ipm_solve_batched"]:
         assert must in names
 
 
@@ -53,6 +53,15 @@ def test_library_loads_and_reports_errors_without_gpu(lib_path):
     assert e.value.code == 1 and "2^a" in str(e.value)
     h = ctypes.c_void_p()
     assert lib.ot_mesh_create(None, ctypes.byref(h)) == 1
+    assert b"NULL" in lib.ot_last_error()
+    # batched: argument checks come before any device work
+    assert lib.ot_ipm_solve_batched(0, None, None, None, None, 1.0, 1e-6, ctypes.byref(o), None, None, None,
+                                    None, None, None, 4) == 0
+    assert lib.ot_ipm_solve_batched(1, None, None, None, None, 1.0, 1e-6, ctypes.byref(o), None, None, None,
+                                    None, None, None, 0) == 1
+    assert b"n_streams" in lib.ot_last_error()
+    assert lib.ot_ipm_solve_batched(1, None, None, None, None, 1.0, 1e-6, ctypes.byref(o), None, None, None,
+                                    None, None, None, 2) == 1
     assert b"NULL" in lib.ot_last_error()
 
 

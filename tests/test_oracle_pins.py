@@ -275,3 +275,70 @@ def test_translation_costs_converge():
     e_x = [abs(out[n, "x"] / (0.08 * 4 / 3) - 1) for n in (4, 8)]
     assert e_diag[1] < e_diag[0] < 0.1 and e_diag[1] < 0.03
     assert e_x[1] < e_x[0] < 0.1 and e_x[1] < 0.03
+
+
+# ----------------------------------------------------------------- adjoint gradient
+def _adjoint_case(gap_tol):
+    from ot_inputs import mixture_params
+
+    n, K = 3, 3
+    d = ipm.discretise(n, K)
+    r0 = make_density(n, *mixture_params(1, 2), 1e-2)
+    r1 = make_density(n, *mixture_params(51, 2), 1e-2)
+    opt = ipm.IPMOptions(gap_tol=gap_tol, final_newton_tol=1e-13)
+    return d, r0, r1, opt, ipm.ipm_solve(d, r0, r1, opt)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """dC/d(rho_in, rho_f) by one transposed-Jacobian solve equals central
+    differences of the converged IPM cost along mass-preserving directions
+    (h = 1e-6, both runs ending at the same mu with ||F|| <= 1e-13)."""
+    from oracle import adjoint
+
+    d, r0, r1, opt, res = _adjoint_case(1e-4)
+    g0, g1 = adjoint.cost_gradient(d, res.phi, res.rho, res.s, r0, r1)
+    rng = np.random.default_rng(8)
+    a = d.t.coarse.area
+    h = 1e-6
+    for which in (0, 1):
+        for _ in range(2):
+            v = rng.uniform(-1, 1, d.Nc)
+            v -= (a @ v) / a.sum()
+            args_p = (r0 + h * v, r1) if which == 0 else (r0, r1 + h * v)
+            args_m = (r0 - h * v, r1) if which == 0 else (r0, r1 - h * v)
+            fd = (ipm.ipm_solve(d, *args_p, opt).cost - ipm.ipm_solve(d, *args_m, opt).cost) / (2 * h)
+            ad = float((g0 if which == 0 else g1) @ v)
+            assert abs(fd - ad) <= 1e-6 * abs(fd), (which, fd, ad)
+
+
+def test_adjoint_gradient_approaches_dual_potential_as_mu_vanishes():
+    """The adjoint gradient tends to the envelope form read off the dual value
+    (-J^T M phi^1 - dt/4 R_E^T W (grad phi^1)^2 at t = 0, and its mirror at
+    t = 1) at rate O(mu): two decades of mu shrink the gap by >= 20x."""
+    from oracle import adjoint
+
+    errs = []
+    for tol in (1e-4, 1e-6):
+        d, r0, r1, opt, res = _adjoint_case(tol)
+        g0, g1 = adjoint.cost_gradient(d, res.phi, res.rho, res.s, r0, r1)
+        e0, e1 = adjoint.envelope_gradient(d, res.phi)
+        errs.append(max(np.linalg.norm(g0 - e0) / np.linalg.norm(g0), np.linalg.norm(g1 - e1) / np.linalg.norm(g1)))
+    assert errs[1] < errs[0] / 20 and errs[1] < 1e-3, errs
+
+
+def test_adjoint_partials_match_finite_differences_of_cost():
+    """The explicit partials dC/du and dC/dr (reading R15) against central
+    differences of ipm.cost at a random point."""
+    from oracle import adjoint
+
+    d = ipm.discretise(2, 2)
+    phi, rho, s, r0, r1 = _random_state(d, 9)
+    dphi, drho, d0, d1 = adjoint.cost_partials(d, phi, rho, r0, r1)
+    h = 1e-6
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        vp, vr, v0, v1 = (rng.standard_normal(x.size) for x in (phi, rho, r0, r1))
+        fd = (ipm.cost(d, phi + h * vp, rho + h * vr, r0 + h * v0, r1 + h * v1)
+              - ipm.cost(d, phi - h * vp, rho - h * vr, r0 - h * v0, r1 - h * v1)) / (2 * h)
+        an = dphi @ vp + drho @ vr + d0 @ v0 + d1 @ v1
+        assert abs(fd - an) < 1e-7 * max(1.0, abs(fd))
