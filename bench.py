@@ -264,18 +264,15 @@ def run_ours(args, world, rank, local):
         bopt = capi.default_options(precision=args.precision)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        try:
-            bout = capi.ot_ipm_solve_batched(items, options=bopt, n_streams=args.batched_streams)
-        except capi.OTError as e:
-            bout = None
-            batched = {"error": str(e)}
+        bout = capi.ot_ipm_solve_batched(items, options=bopt, n_streams=args.batched_streams, raise_on_error=False)
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
-    if not args.no_batched and bout is not None:
+        failed = [i for i, o in enumerate(bout) if o["status"] != 0]
         batched = {"workload": "64 problems, side in {16,24,32,48,64}, K in {8,16,24,32}, 1-4 Gaussians, "
                                "floor 1e-4 (seeds 1000..1063)",
                    "precision": args.precision, "n_streams": args.batched_streams, "seconds": tb,
-                   "problems_per_s": len(items) / tb,
+                   "problems_per_s": len(items) / tb, "converged": len(items) - len(failed),
+                   "failed": {i: capi.STATUS.get(bout[i]["status"], bout[i]["status"]) for i in failed},
                    "newton_steps": sum(o["stats"]["newton_steps"] for o in bout),
                    "unknowns": sum((K_ + 1) * 8 * n_ * n_ + K_ * 2 * n_ * n_ for n_, K_, _, _ in specs)}
 

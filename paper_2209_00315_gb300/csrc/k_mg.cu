@@ -185,9 +185,22 @@ __device__ __forceinline__ void pcr_solve(T (&a)[KPL], T (&d)[KPL], T (&c)[KPL],
   }
 }
 
-// Line update of cell c (same system as line_gs) by one warp.
-template <typename T, int KPL>
-__device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, int lane) {
+// Sweep modes of the smoothers (see k_mg_smooth_mode).
+enum { kSweepPlain = 0, kSweepFromZero = 1, kSweepAfterProlong = 2 };
+
+// Value of the spatial neighbour o of slice k as the sweep sees it.
+template <typename T, int MODE>
+__device__ __forceinline__ T sweep_neighbour(const LevelView<T>& L, const LevelView<T>& Lc, int k, int o) {
+  if (MODE == kSweepFromZero) return (T)0;
+  T v = L.x[(i64)k * L.ld + o];
+  if (MODE == kSweepAfterProlong) v += Lc.x[(i64)k * Lc.ld + parent_of(L.m, o)];
+  return v;
+}
+
+// Line update of cell c (same system as line_gs) by one warp; neighbour
+// values as the sweep mode gives them.
+template <typename T, int KPL, int MODE>
+__device__ __forceinline__ void line_pcr_mode(int S, const LevelView<T>& L, const LevelView<T>& Lc, i64 c, int lane) {
   i64 nb[3];
   neighbours(L.m, decode(L.m, c), nb);
   T a[KPL], d[KPL], cc[KPL], r[KPL];
@@ -202,7 +215,7 @@ __device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, in
       for (int sl = 0; sl < 3; ++sl) {
         T al = L.alpha[((i64)sl * S + k) * L.ld + c];
         dg += al;
-        if (nb[sl] >= 0) rhs += al * L.x[o + nb[sl]];
+        if (MODE != kSweepFromZero && nb[sl] >= 0) rhs += al * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
       }
       d[q] = dg;
       r[q] = rhs;
@@ -221,6 +234,26 @@ __device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, in
 }
 
 template <typename T, int KPL>
+__device__ __forceinline__ void line_pcr(int S, const LevelView<T>& L, i64 c, int lane) {
+  line_pcr_mode<T, KPL, kSweepPlain>(S, L, L, c, lane);
+}
+
+// Point update of cell c in slice k with the sweep mode's neighbour values.
+template <typename T, int MODE>
+__device__ __forceinline__ void point_gs_mode(int S, const LevelView<T>& L, const LevelView<T>& Lc, int k, int c) {
+  i64 nb[3];
+  neighbours(L.m, decode(L.m, c), nb);
+  T num = L.b[(i64)k * L.ld + c], den = 0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    T a = L.alpha[((i64)sl * S + k) * L.ld + c];
+    den += a;
+    if (MODE != kSweepFromZero && nb[sl] >= 0) num += a * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
+  }
+  L.x[(i64)k * L.ld + c] = mg_div(num, den);
+}
+
+template <typename T, int KPL>
 __global__ void __launch_bounds__(256) k_line_pcr_kernel(int S, LevelView<T> L, int color) {
   i64 sq = (i64)L.m * L.m;
   int lane = threadIdx.x & 31;
@@ -236,18 +269,6 @@ static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128
 // into a padded [K][9] shared tile, warp w solves column w by PCR, and the
 // solutions leave through the same tile.
 constexpr int kTileCells = 8;
-// Sweep modes of the large-level smoothers (see k_mg_smooth_mode).
-enum { kSweepPlain = 0, kSweepFromZero = 1, kSweepAfterProlong = 2 };
-
-// Value of the spatial neighbour o of slice k as the sweep sees it.
-template <typename T, int MODE>
-__device__ __forceinline__ T sweep_neighbour(const LevelView<T>& L, const LevelView<T>& Lc, int k, int o) {
-  if (MODE == kSweepFromZero) return (T)0;
-  T v = L.x[(i64)k * L.ld + o];
-  if (MODE == kSweepAfterProlong) v += Lc.x[(i64)k * Lc.ld + parent_of(L.m, o)];
-  return v;
-}
-
 template <typename T, int KPL, int MODE>
 __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
   constexpr int P = kTileCells + 1;
@@ -362,19 +383,7 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
 template <typename T, int MODE>
 __global__ void k_point_smooth_mode_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
   const int sq = L.m * L.m;
-  SLICE_LOOP(k, S, i, sq) {
-    const int c = color * sq + (int)i;
-    i64 nb[3];
-    neighbours(L.m, decode(L.m, c), nb);
-    T num = L.b[(i64)k * L.ld + c], den = 0;
-#pragma unroll
-    for (int sl = 0; sl < 3; ++sl) {
-      T a = L.alpha[((i64)sl * S + k) * L.ld + c];
-      den += a;
-      if (MODE != kSweepFromZero && nb[sl] >= 0) num += a * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
-    }
-    L.x[(i64)k * L.ld + c] = mg_div(num, den);
-  }
+  SLICE_LOOP(k, S, i, sq) point_gs_mode<T, MODE>(S, L, Lc, k, color * sq + (int)i);
 }
 
 template <typename T>
@@ -716,25 +725,34 @@ __global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, Le
   __shared__ LevelSet<T> ls;
   stage_levels(gls, ls, reinterpret_cast<T*>(smem_raw), S, 1, k);
   const int last = ls.n - 1;
+  // (the first sweep of a level reads zero neighbours, so x needs no reset,
+  // except on the coarsest level and when there are no sweeps)
   for (int l = 0; l <= last; ++l) {
     const LevelView<T>& L = ls.L[l];
     const int sq = L.m * L.m, nc = (int)L.nc;
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) L.x[i] = 0;
-    __syncthreads();
     const int sweeps = (l == last) ? nuc : nu;
+    if (sweeps == 0) {
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) L.x[i] = 0;
+      __syncthreads();
+    }
     for (int it = 0; it < sweeps; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
+        if (it == 0 && col == 0)
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_mode<T, kSweepFromZero>(1, L, L, 0, i);
+        else
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
         __syncthreads();
       }
     if (l == last) break;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) L.r[c] = L.b[c] - level_apply(1, L, 0, c);
-    __syncthreads();
+    // b_coarse = J^T (b - M x) in one phase
     const LevelView<T>& Lc = ls.L[l + 1];
     for (int C = threadIdx.x; C < (int)Lc.nc; C += blockDim.x) {
       i64 ch[4];
       children(Lc.m, decode(Lc.m, C), ch);
-      Lc.b[C] = L.r[ch[0]] + L.r[ch[1]] + L.r[ch[2]] + L.r[ch[3]];
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += L.b[ch[a]] - level_apply(1, L, 0, ch[a]);
+      Lc.b[C] = acc;
     }
     __syncthreads();
   }
@@ -742,11 +760,16 @@ __global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, Le
     const LevelView<T>& L = ls.L[l];
     const LevelView<T>& Lc = ls.L[l + 1];
     const int sq = L.m * L.m, nc = (int)L.nc;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) L.x[c] += Lc.x[parent_of(L.m, c)];
-    __syncthreads();
+    if (nu == 0) {
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) L.x[c] += Lc.x[parent_of(L.m, c)];
+      __syncthreads();
+    }
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
-        for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
+        if (it == 0 && col == 1)
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_mode<T, kSweepAfterProlong>(1, L, Lc, 0, sq + i);
+        else
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
         __syncthreads();
       }
   }
@@ -768,23 +791,30 @@ __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kerne
   const int last = ls.n - 1;
   for (int l = 0; l < last; ++l) {
     const LevelView<T>& L = ls.L[l];
-    const int sq = L.m * L.m, nc = (int)L.nc, ld = (int)L.ld;
-    for (int i = threadIdx.x; i < S * ld; i += blockDim.x) L.x[i] = 0;
-    __syncthreads();
+    const int sq = L.m * L.m, ld = (int)L.ld;
+    if (nu == 0) {
+      for (int i = threadIdx.x; i < S * ld; i += blockDim.x) L.x[i] = 0;
+      __syncthreads();
+    }
     for (int it = 0; it < nu; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
+        if (it == 0 && col == 0)
+          for (int w = warp; w < sq; w += nwarp) line_pcr_mode<T, KPL, kSweepFromZero>(S, L, L, (i64)w, lane);
+        else
+          for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
         __syncthreads();
       }
-    for (SliceWalk w(nc); w.k < S; w.next()) L.r[w.k * ld + w.c] = L.b[w.k * ld + w.c] - level_apply(S, L, w.k, w.c);
-    __syncthreads();
+    // b_coarse = J^T (b - M x) in one phase
     const LevelView<T>& Lc = ls.L[l + 1];
     const int ldc = (int)Lc.ld;
     for (SliceWalk w((int)Lc.nc); w.k < S; w.next()) {
       i64 ch[4];
       children(Lc.m, decode(Lc.m, w.c), ch);
-      const T* rf = L.r + w.k * ld;
-      Lc.b[w.k * ldc + w.c] = rf[ch[0]] + rf[ch[1]] + rf[ch[2]] + rf[ch[3]];
+      const T* bf = L.b + w.k * ld;
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += bf[ch[a]] - level_apply(S, L, w.k, ch[a]);
+      Lc.b[w.k * ldc + w.c] = acc;
     }
     __syncthreads();
   }
@@ -794,11 +824,16 @@ __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kerne
     const LevelView<T>& L = ls.L[l];
     const LevelView<T>& Lc = ls.L[l + 1];
     const int sq = L.m * L.m, nc = (int)L.nc, ld = (int)L.ld, ldc = (int)Lc.ld;
-    for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] += Lc.x[w.k * ldc + (int)parent_of(L.m, w.c)];
-    __syncthreads();
+    if (nu == 0) {
+      for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] += Lc.x[w.k * ldc + (int)parent_of(L.m, w.c)];
+      __syncthreads();
+    }
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
-        for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
+        if (it == 0 && col == 1)
+          for (int w = warp; w < sq; w += nwarp) line_pcr_mode<T, KPL, kSweepAfterProlong>(S, L, Lc, (i64)(sq + w), lane);
+        else
+          for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
         __syncthreads();
       }
   }

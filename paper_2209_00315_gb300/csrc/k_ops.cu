@@ -121,9 +121,14 @@ void k_kkt_coef(const Dims& d, const double* phi, const double* rho, const doubl
   launch(k_kkt_sr_kernel, nblk((i64)d.K * d.Nc), kT, 0, cs(st), d, rho, s, kc + (i64)(d.K + 1) * 6 * d.N);
 }
 
-__global__ void k_kkt_phi_cached_kernel(Dims d, const double* kc, const double* xp, const double* xr,
-                                        const double* xmean, bool with_a, double* y) {
-  SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi_cached(d, kc, xp, xr, xmean, with_a, jj, c);
+// Slice values of the B^T part (kkt_slice_values) into the scratch of kc.
+__global__ void k_kkt_slice_values_kernel(Dims d, const double* xr, const double* xmean, double* yb) {
+  SLICE_LOOP(jj, d.K + 1, C, d.Nc) kkt_slice_values(d, xr, xmean, jj, C, yb);
+}
+
+__global__ void k_kkt_phi_sliced_kernel(Dims d, const double* kc, const double* xp, const double* yb, bool with_a,
+                                        double* y) {
+  SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi_sliced(d, kc, xp, yb, with_a, jj, c);
 }
 
 __global__ void k_kkt_rho_cached_kernel(Dims d, const double* kc, const double* xp, const double* xr,
@@ -140,9 +145,10 @@ void k_kkt_apply(const Dims& d, const double* kc, const double* x, double* y, do
   i64 Np = (i64)(d.K + 1) * d.N;
   const double* xr = x + Np;
   prof::begin(prof::KKT, st);
+  double* yb = const_cast<double*>(kc) + kkt_yb_offset(d);
   launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), xr, d.Nc, xmean);
-  launch(k_kkt_phi_cached_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, x, xr, (const double*)xmean, true,
-         y);
+  launch(k_kkt_slice_values_kernel, slice_grid(d.Nc, d.K + 1), kT, 0, cs(st), d, xr, (const double*)xmean, yb);
+  launch(k_kkt_phi_sliced_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, x, (const double*)yb, true, y);
   launch(k_kkt_rho_cached_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, kc, x, xr, (const double*)xmean, y + Np);
   launch(k_project_kernel, d.K, 1024, 0, cs(st), y + Np, d.Nc, wsum);
   // x, y on both blocks, the six edge coefficients per fine cell and |C| s/rho
@@ -185,8 +191,10 @@ void k_bt_apply(const Dims& d, const double* kc, const double* yr, double* out_p
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);
   launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), yr, d.Nc, yr_mean);
-  launch(k_kkt_phi_cached_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, (const double*)nullptr, yr,
-         (const double*)yr_mean, false, out_phi);
+  double* yb = const_cast<double*>(kc) + kkt_yb_offset(d);
+  launch(k_kkt_slice_values_kernel, slice_grid(d.Nc, d.K + 1), kT, 0, cs(st), d, yr, (const double*)yr_mean, yb);
+  launch(k_kkt_phi_sliced_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, (const double*)nullptr,
+         (const double*)yb, false, out_phi);
   prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc + 3.0 * Np));
 }
 

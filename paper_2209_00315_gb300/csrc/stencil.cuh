@@ -47,6 +47,7 @@ struct Dims {
   i64 N, Nc;            // fine / coarse cells per slice
   double dt;            // 1/(K+1)
   double area_f, area_c;
+  double af_dt;         // area_f / dt
 };
 
 OT_HD Dims make_dims(int n, int K) {
@@ -59,6 +60,7 @@ OT_HD Dims make_dims(int n, int K) {
   d.dt = 1.0 / (K + 1);
   d.area_c = 0.5 / ((double)n * n);
   d.area_f = 0.5 / ((double)d.m * d.m);
+  d.af_dt = d.area_f / d.dt;
   return d;
 }
 
@@ -283,8 +285,11 @@ OT_HD T kkt_rho(const Dims& d, const T* phi, const T* rho, const T* s, const T* 
 //   kc[(jj*6 + sl)*N + c]     = w = T_e (rho~_c + rho~_o)/2,
 //   kc[(jj*6 + 3 + sl)*N + c] = g = T_e (phi^jj_c - phi^jj_o)/2   (zero on boundary slots),
 //   kc[(K+1)*6*N + k0*N' + C] = |C| s/rho,
-// every later operator application is loads plus a few FMAs per row.
-OT_HD i64 kkt_coef_count(const Dims& d) { return (i64)(d.K + 1) * 6 * d.N + (i64)d.K * d.Nc; }
+// every later operator application is loads plus a few FMAs per row.  The
+// 2(K+1)N' values after those are scratch of each application (the slice
+// values of kkt_slice_values).
+OT_HD i64 kkt_yb_offset(const Dims& d) { return (i64)(d.K + 1) * 6 * d.N + (i64)d.K * d.Nc; }
+OT_HD i64 kkt_coef_count(const Dims& d) { return kkt_yb_offset(d) + 2LL * (d.K + 1) * d.Nc; }
 
 OT_HD void kkt_edge_coef(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
                          int jj, i64 c, double w[3], double g[3]) {
@@ -307,29 +312,37 @@ OT_HD void kkt_edge_coef(const Dims& d, const double* phi, const double* rho, co
   }
 }
 
-// kkt_phi from the edge coefficients (with_a = false: the B^T P^T part only).
-OT_HD double kkt_phi_cached(const Dims& d, const double* kc, const double* xp, const double* xr,
-                            const double* xmean, bool with_a, int jj, i64 c) {
+// The B^T P^T part of the phi rows depends on x_rho only through, per
+// potential slice jj and coarse cell C (y = x_rho minus its slice means,
+// y^{-1} = y^{K} = 0 at the ends):
+//   ybar^jj_C  = (y^{jj-1}_C + y^jj_C)/2,   ydif^jj_C = |c| (y^{jj-1}_C - y^jj_C)/dt.
+// yb holds ybar for jj = 0..K, then ydif.
+OT_HD void kkt_slice_values(const Dims& d, const double* xr, const double* xmean, int jj, i64 C, double* yb) {
+  const double ym = (jj >= 1) ? xr[(i64)(jj - 1) * d.Nc + C] - xmean[jj - 1] : 0.0;
+  const double yp = (jj <= d.K - 1) ? xr[(i64)jj * d.Nc + C] - xmean[jj] : 0.0;
+  yb[(i64)jj * d.Nc + C] = 0.5 * (ym + yp);
+  yb[(i64)(d.K + 1 + jj) * d.Nc + C] = d.af_dt * (ym - yp);
+}
+
+// kkt_phi from the edge coefficients and the slice values of kkt_slice_values
+// (with_a = false: the B^T P^T part only): three FMA pairs per row.
+OT_HD double kkt_phi_sliced(const Dims& d, const double* kc, const double* xp, const double* yb, bool with_a,
+                            int jj, i64 c) {
   Cell q = decode(d.m, c);
   i64 nb[3];
   Cell nq[3];
   neighbours(d.m, q, nb, nq);
-  i64 P = parent(d.m, q);
+  const i64 P = parent(d.m, q);
+  const double* ybar = yb + (i64)jj * d.Nc;
   const double* xs = xp + (i64)jj * d.N;
-  const double* ym = (jj >= 1) ? xr + (i64)(jj - 1) * d.Nc : nullptr;
-  const double* yp = (jj <= d.K - 1) ? xr + (i64)jj * d.Nc : nullptr;
-  double mm = (jj >= 1) ? xmean[jj - 1] : 0.0, mp = (jj <= d.K - 1) ? xmean[jj] : 0.0;
-  double yma = ym ? ym[P] - mm : 0.0, ypa = yp ? yp[P] - mp : 0.0;
-  double acc = d.area_f * (yma - ypa) / d.dt;
-  double ybc = 0.5 * (yma + ypa);
-  double xc = with_a ? xs[c] : 0.0;
+  double acc = yb[(i64)(d.K + 1 + jj) * d.Nc + P];
+  const double ybc = ybar[P];
+  const double xc = with_a ? xs[c] : 0.0;
   const double* kw = kc + (i64)jj * 6 * d.N + c;
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     if (nb[sl] < 0) continue;
-    i64 Po = parent(d.m, nq[sl]);
-    double ybo = 0.5 * ((ym ? ym[Po] - mm : 0.0) + (yp ? yp[Po] - mp : 0.0));
-    acc += kw[(i64)(3 + sl) * d.N] * (ybc + ybo);
+    acc += kw[(i64)(3 + sl) * d.N] * (ybc + ybar[parent(d.m, nq[sl])]);
     if (with_a) acc += kw[(i64)sl * d.N] * (xc - xs[nb[sl]]);
   }
   return acc;
@@ -343,21 +356,22 @@ OT_HD double apply_B_cached(const Dims& d, const double* kc, const double* x, in
   const double* x1 = x0 + d.N;
   const double* g0 = kc + ((i64)k0 * 6 + 3) * d.N;
   const double* g1 = kc + ((i64)(k0 + 1) * 6 + 3) * d.N;
-  double acc = 0.0;
+  double dtime = 0.0, edges = 0.0;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     i64 c = ch[a];
     i64 nb[3];
     neighbours(d.m, decode(d.m, c), nb);
-    acc += d.area_f * (x1[c] - x0[c]) / d.dt;
+    const double x0c = x0[c], x1c = x1[c];
+    dtime += x1c - x0c;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
       if (nb[sl] < 0) continue;
       i64 o = nb[sl];
-      acc += 0.5 * (g0[(i64)sl * d.N + c] * (x0[c] - x0[o]) + g1[(i64)sl * d.N + c] * (x1[c] - x1[o]));
+      edges += g0[(i64)sl * d.N + c] * (x0c - x0[o]) + g1[(i64)sl * d.N + c] * (x1c - x1[o]);
     }
   }
-  return acc;
+  return d.af_dt * dtime + 0.5 * edges;
 }
 
 // ----------------------------------------------------------------- BB pieces

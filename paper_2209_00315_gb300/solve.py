@@ -24,6 +24,8 @@ def main(argv=None):
     p.add_argument("--repeat", type=int, default=1)
     p.add_argument("--tol", type=float, default=1e-6, help="duality-gap target")
     p.add_argument("--verbose", action="store_true", help="print one line per barrier stage")
+    p.add_argument("--restart", type=int, default=None, help="FGMRES restart length")
+    p.add_argument("--max-iter", type=int, default=None, help="FGMRES iteration cap per Newton step")
     a = p.parse_args(argv)
 
     from ot_inputs import config_densities
@@ -32,7 +34,12 @@ def main(argv=None):
     mesh = capi.Mesh(n)
     r0d = torch.from_numpy(r0).cuda()
     r1d = torch.from_numpy(r1).cuda()
-    opt = capi.default_options(precision=a.precision, verbose=int(a.verbose))
+    extra = {}
+    if a.restart is not None:
+        extra["fgmres_restart"] = a.restart
+    if a.max_iter is not None:
+        extra["fgmres_max_iter"] = a.max_iter
+    opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
     walls, res = [], None
     for _ in range(a.repeat):
         torch.cuda.synchronize()
@@ -45,6 +52,7 @@ def main(argv=None):
         "workload": a.workload, "n": n, "K": K, "precision": a.precision, "cost": res["cost"],
         "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"], "inner_iters": st["inner_iters"],
         "gap": st["gap"], "wall_s": walls, "kernel_launches": capi.ot_kernel_launches(),
+        "fgmres_restart": opt.fgmres_restart, "fgmres_max_iter": opt.fgmres_max_iter,
     }))
 
 

@@ -208,3 +208,37 @@ def test_errors_are_returned_not_raised_on_device(gpu_lib):
     # the context is still usable afterwards
     res = capi.ot_ipm_solve(mesh, T(good), T(good), K)
     assert abs(res["cost"]) < 1e-20
+
+
+@pytest.mark.slow
+def test_full_size_mix64_against_oracle_properties(gpu_lib):
+    """The benchmark workload (64x64 squares, K = 32, mixed precision, default
+    options, as bench.py runs it) checked with the oracle at full size, through
+    properties the oracle evaluates directly: its residual at the GPU solution
+    meets the final Newton tolerance, its cost and dual value reproduce the
+    GPU's, the duality gap is mu |Omega| K/(K+1), masses are conserved slice by
+    slice, and rho, s > 0."""
+    from paper_2209_00315_gb300 import capi
+
+    n, K, r0, r1 = config_densities("mix64")
+    mesh = capi.Mesh(n)
+    res = capi.ot_ipm_solve(mesh, T(r0), T(r1), K, options=capi.default_options(precision="mixed"))
+    st = res["stats"]
+    d = ipm.discretise(n, K)
+    phi, rho, s = (res[k].cpu().numpy() for k in ("phi", "rho", "s"))
+    mu = st["mu"]
+    F = ipm.residual(d, phi, rho, s, r0, r1, mu)
+    fn = ipm.residual_norm(F)
+    # the oracle's ||F|| at the returned point is the GPU's own final ||F||, which met R6
+    assert abs(fn - st["final_residual"]) <= 1e-6 * st["final_residual"] + 1e-13, (fn, st["final_residual"])
+    assert fn < 1e-6
+    c = ipm.cost(d, phi, rho, r0, r1)
+    dv = ipm.dual_value(d, phi, r0, r1)
+    assert abs(c - res["cost"]) < 1e-12 * c
+    assert abs(dv - st["dual"]) < 1e-10 * max(1.0, abs(dv))
+    # C - D = mu |Omega| K/(K+1) holds exactly at F = 0; here up to the Newton tolerance
+    gap = mu * d.area_total * K / (K + 1)
+    assert abs((c - dv) - gap) < 0.05 * gap, (c - dv, gap)
+    mass = d.rho_slices(rho) @ d.t.coarse.area
+    assert np.abs(mass - d.t.coarse.area @ r0).max() < 1e-12
+    assert rho.min() > 0 and s.min() > 0
