@@ -71,7 +71,7 @@ typedef enum { OT_PREC_FP64 = 0, OT_PREC_MIXED = 1 } ot_precision;
 /* Solver options; ot_default_options() fills the values used by the paper. */
 typedef struct {
   int32_t memspace;         /* OT_MEM_DEVICE or OT_MEM_HOST */
-  int32_t precision;        /* OT_PREC_FP64: everything FP64; OT_PREC_MIXED: FP32 multigrid */
+  int32_t precision;        /* OT_PREC_FP64: everything FP64; OT_PREC_MIXED: the BB preconditioner in FP32 */
   double mu_factor;         /* mu_{l+1} = mu_factor mu_l (0.2) */
   double tau;               /* fraction to the boundary (0.99) */
   double newton_tol;        /* Newton stop: ||F|| <= newton_tol max(1, ||F_stage_start||) (1e-6) */
@@ -79,7 +79,9 @@ typedef struct {
   double eps_out;           /* FGMRES: ||r|| <= eps_out ||(f;g;h)|| (1e-5, Sec. 3.1) */
   double final_eps_out;     /* the same in the last stage; <= 0: eps_out */
   double eps_schur;         /* inner Schur solve relative tolerance (1e-1, Sec. 4.3.3) */
-  int32_t fgmres_restart;   /* restart length (30) */
+  int32_t fgmres_restart;   /* restart length; 0 (default): automatic = no restart up to fgmres_max_iter,
+                               as far as the 2m+1 Krylov vectors fit 64 GiB (96 GiB shared by the streams
+                               of a batched call), never below 30; max 800 */
   int32_t fgmres_max_iter;  /* total FGMRES iterations per linear system (400) */
   int32_t schur_max_iter;   /* inner GMRES iterations per preconditioner application */
   int32_t lap_cycles;       /* multigrid V-cycles per time-slice Laplacian solve */

@@ -65,7 +65,7 @@ void ot_default_options(ot_options* o) {
   o->eps_out = 1e-5;
   o->final_eps_out = 0.0;
   o->eps_schur = 1e-1;
-  o->fgmres_restart = 30;
+  o->fgmres_restart = 0;  // automatic: no restart up to the cap, within the Krylov memory budget
   o->fgmres_max_iter = 400;
   o->schur_max_iter = 20;
   o->lap_cycles = 2;     // two V(2,2) cycles: ~5e-2 relative residual, the paper's Laplacian tolerance
@@ -96,7 +96,8 @@ static ot_options resolve(const ot_options* o) {
   require(r.mu_factor > 0 && r.mu_factor < 1, "options.mu_factor must be in (0, 1)");
   require(r.tau > 0 && r.tau < 1, "options.tau must be in (0, 1)");
   require(r.newton_tol > 0 && r.eps_out > 0 && r.eps_schur > 0, "tolerances must be positive");
-  require(r.fgmres_restart >= 1 && r.fgmres_restart <= 480, "options.fgmres_restart must be in [1, 480]");
+  require(r.fgmres_restart >= 0 && r.fgmres_restart <= ot::kMaxRestart,
+          "options.fgmres_restart must be in [0, 800] (0: automatic)");
   require(r.fgmres_max_iter >= 1, "options.fgmres_max_iter");
   require(r.schur_max_iter >= 1 && r.schur_max_iter <= 480, "options.schur_max_iter must be in [1, 480]");
   require(r.lap_cycles >= 1 && r.smooth_sweeps >= 0 && r.coarse_sweeps >= 1, "multigrid cycle counts");
@@ -110,7 +111,8 @@ static Workspace& workspace(ot_mesh* m, int K, const ot_options& o) {
   auto key = std::make_pair(K, o.precision);
   auto it = m->ws.find(key);
   if (it != m->ws.end() &&
-      (it->second->cur_restart < o.fgmres_restart || it->second->cur_inner < o.schur_max_iter))
+      (it->second->cur_restart < ot::effective_restart(o, it->second->ntot) ||
+       it->second->cur_inner < o.schur_max_iter))
     m->ws.erase(it), it = m->ws.end();
   if (it == m->ws.end()) {
     auto w = std::unique_ptr<Workspace>(new Workspace(m->n, K, o.precision, o));
@@ -283,25 +285,31 @@ ot_status ot_ipm_solve_batched(int32_t n_prob, ot_mesh* const* meshes, const int
   std::atomic<int> next{0};
   std::vector<int> codes(n_prob, OT_OK);
   std::vector<std::string> msgs(n_prob);
+  // the streams share one Krylov memory budget
+  const size_t budget = ((size_t)96 << 30) / (size_t)std::min<int>(n_streams, n_prob);
   auto worker = [&]() {
     ot::prof::suspended = true;
+    dev::set_krylov_budget(budget);
     Stream stream = nullptr;
     try {
       dev::set_device(device);
       stream = dev::stream_create();
+      dev::set_alloc_stream(stream);
     } catch (const std::exception& e) {
       for (int i; (i = next.fetch_add(1)) < n_prob;) codes[order[i]] = OT_ERR_CUDA, msgs[order[i]] = e.what();
       return;
     }
-    // this thread's workspaces, one per (side, K)
+    // this thread's workspace, replaced when the next problem's (side, K) differs
     std::map<std::pair<int, int>, std::unique_ptr<Workspace>> mine;
     for (int i; (i = next.fetch_add(1)) < n_prob;) {
       const int p = order[i];
       try {
         auto key = std::make_pair(meshes[p]->n, (int)K[p]);
         auto it = mine.find(key);
-        if (it == mine.end())
+        if (it == mine.end()) {
+          mine.clear();
           it = mine.emplace(key, std::unique_ptr<Workspace>(new Workspace(meshes[p]->n, K[p], o.precision, o))).first;
+        }
         solve_in(*it->second, meshes[p], rho_in[p], rho_f[p], mu0, tol, o, 0, rho[p], phi[p], s[p],
                  cost ? cost + p : nullptr, stats ? stats + p : nullptr, stream);
       } catch (const ot::Error& e) {
@@ -314,6 +322,8 @@ ot_status ot_ipm_solve_batched(int32_t n_prob, ot_mesh* const* meshes, const int
     }
     dev::sync_quiet(stream);
     mine.clear();
+    dev::sync_quiet(stream);
+    dev::set_alloc_stream(nullptr);
     dev::stream_destroy(stream);
   };
   const int nt = std::min<int>(n_streams, n_prob);

@@ -98,10 +98,19 @@ void read(int id, double* ms, long long* n, double* b) {
 }  // namespace prof
 
 namespace dev {
+// Threads that drive their own stream allocate stream-ordered from the
+// device's memory pool: no device-wide synchronisation on free, and freed
+// blocks are reused by the next workspace.
+static thread_local cudaStream_t t_alloc_stream = nullptr;
+void set_alloc_stream(Stream s) { t_alloc_stream = cs(s); }
+static thread_local size_t t_krylov_budget = (size_t)64 << 30;
+size_t krylov_budget() { return t_krylov_budget; }
+void set_krylov_budget(size_t bytes) { t_krylov_budget = bytes; }
+
 void* alloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = t_alloc_stream ? cudaMallocAsync(&p, bytes, t_alloc_stream) : cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     char buf[160];
@@ -111,7 +120,11 @@ void* alloc(size_t bytes) {
   return p;
 }
 void release(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  if (t_alloc_stream)
+    cudaFreeAsync(p, t_alloc_stream);
+  else
+    cudaFree(p);
 }
 void* host_alloc(size_t bytes) {
   void* p = nullptr;

@@ -25,6 +25,12 @@ struct Error : std::runtime_error {
 
 namespace dev {
 void* alloc(size_t bytes);                       // throws Error(OT_ERR_OOM)
+// This thread's later alloc/release become stream-ordered on s (null: plain).
+void set_alloc_stream(Stream s);
+// Bytes the outer Krylov basis of one solve may take on this thread (64 GiB
+// unless set; concurrent solves share a budget).
+size_t krylov_budget();
+void set_krylov_budget(size_t bytes);
 void release(void* p);
 void* host_alloc(size_t bytes);                  // pinned
 void host_release(void* p);

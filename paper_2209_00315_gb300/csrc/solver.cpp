@@ -107,6 +107,14 @@ template struct KrylovT<double>;
 
 static double* dalloc(i64 n) { return (double*)dev::alloc(sizeof(double) * (size_t)(n > 0 ? n : 1)); }
 
+int effective_restart(const ot_options& opt, i64 ntot) {
+  if (opt.fgmres_restart > 0) return opt.fgmres_restart;
+  const i64 per_vector = 2 * ntot * (i64)sizeof(double);  // one V and one Z vector
+  const i64 fit = (i64)(dev::krylov_budget() / (size_t)(per_vector > 0 ? per_vector : 1));
+  const i64 cap = std::min<i64>(opt.fgmres_max_iter, kMaxRestart);
+  return (int)std::max<i64>(std::min<i64>(30, cap), std::min<i64>(cap, fit));
+}
+
 Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
   d = make_dims(n, K);
   precision = prec;
@@ -134,13 +142,13 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
     mass = dalloc(K + 2);
     scal = dalloc(64 + 2 * (K + 2));
     kcoef = dalloc(kkt_coef_count(d));
-    int mm = std::max(opt.fgmres_restart, opt.schur_max_iter) + 2;
+    cur_restart = effective_restart(opt, ntot);
+    int mm = std::max(cur_restart, opt.schur_max_iter) + 2;
     partial = dalloc((i64)k_reduce_scratch(mm < 64 ? 64 : mm));
     u = dalloc(Np);
     bphi = dalloc(Np);
     srhs = dalloc(Nr);
     zeta = dalloc(Nr);
-    cur_restart = opt.fgmres_restart;
     cur_inner = opt.schur_max_iter;
     outer.build(cur_restart, ntot);
     if (prec == OT_PREC_MIXED) {
@@ -186,7 +194,8 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
       lapd.build(d.m, K + 1, false);
       schd.build(d.n, K, true);
     }
-    host = (double*)dev::host_alloc(sizeof(double) * 1024);
+    hoff = std::max(cur_restart, cur_inner) + 4;
+    host = (double*)dev::host_alloc(sizeof(double) * (size_t)(2 * hoff + 64));
   } catch (...) {
     this->~Workspace();
     throw;
@@ -342,10 +351,10 @@ static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_a
     k_mupdate(K.V, K.n, j + 1, K.hc2, K.w, K.n, K.hc2, false, true, W.partial, st);
     k_scale_by_inv_norm(K.w, K.hc2 + j + 1, K.V + (i64)(j + 1) * K.n, K.n, st);
     dev::copy_d2h(hb, K.hc1, sizeof(double) * (j + 1), st);
-    dev::copy_d2h(hb + 512, K.hc2, sizeof(double) * (j + 2), st);
+    dev::copy_d2h(hb + W.hoff, K.hc2, sizeof(double) * (j + 2), st);
     dev::sync(st);
-    for (int i = 0; i <= j; ++i) h(i, j) = hb[i] + hb[512 + i];
-    double hn = sqrt(std::max(hb[512 + j + 1], 0.0));
+    for (int i = 0; i <= j; ++i) h(i, j) = hb[i] + hb[W.hoff + i];
+    double hn = sqrt(std::max(hb[W.hoff + j + 1], 0.0));
     h(j + 1, j) = hn;
     for (int i = 0; i < j; ++i) {
       double a = h(i, j), b = h(i + 1, j);
@@ -382,9 +391,9 @@ static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_a
 template <typename T>
 static double norm2(Workspace& W, const T* x, i64 n, Stream st) {
   k_dot(x, x, n, W.scal + 32, W.partial, st);
-  dev::copy_d2h(W.host + 1000, W.scal + 32, sizeof(double), st);
+  dev::copy_d2h(W.host + 2 * W.hoff, W.scal + 32, sizeof(double), st);
   dev::sync(st);
-  return sqrt(std::max(W.host[1000], 0.0));
+  return sqrt(std::max(W.host[2 * W.hoff], 0.0));
 }
 
 // ------------------------------------------------------------------ BB preconditioner
@@ -464,7 +473,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   int total = 0;
   double res = beta;
   while (true) {
-    int m = std::min(std::min(opt.fgmres_restart, K.mmax), opt.fgmres_max_iter - total);
+    int m = std::min(std::min(effective_restart(opt, n), K.mmax), opt.fgmres_max_iter - total);
     if (m <= 0) break;
     total += arnoldi(W, K, m, beta, tol_abs, prec, op, x, &res, st);
     if (res <= tol_abs || total >= opt.fgmres_max_iter) break;

@@ -81,7 +81,8 @@ struct Workspace {
   BBVectors<float> bbf;
   Hierarchy<float> lapf, schf;
   Hierarchy<double> lapd, schd;
-  double* host = nullptr;     // pinned host scratch (256 doubles)
+  double* host = nullptr;     // pinned host scratch: [0, hoff) and [hoff, 2 hoff) Hessenberg columns, then 64 scalars
+  int hoff = 0;
   // counters of the current call
   long long outer_iters = 0, inner_iters = 0, capped_solves = 0;
   int cur_restart = 0, cur_inner = 0;
@@ -89,6 +90,14 @@ struct Workspace {
   Workspace(int n, int K, int precision, const ot_options& opt);
   ~Workspace();
 };
+
+constexpr int kMaxRestart = 800;
+
+// FGMRES restart length for these options and ntot unknowns: opt.fgmres_restart
+// if > 0; otherwise (automatic) the iteration cap, i.e. no restart as in the
+// paper, as far as the Krylov basis (2m+1 vectors) fits the thread's budget
+// (dev::krylov_budget), never below 30.
+int effective_restart(const ot_options& opt, i64 ntot);
 
 // KKT edge coefficients, level-0 coefficients of both hierarchies and their
 // coarsenings (and the FP32 state copies) from the current (phi, rho, s).
