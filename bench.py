@@ -35,8 +35,9 @@ SAMPLE_N, SAMPLE_K = 12, 6   # bounded sample of the same density recipe for the
 SAMPLE_EVERY = 16            # time one launch in 16 of the roofline kernel inside the timed region
 METRIC = "IPM time-to-solution at duality gap 1e-6"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in profiles/ (None if the
-# kernel changed since it was taken)
-NCU_TRAFFIC = {}
+# kernel changed since it was taken): schur_line_smooth = mean over 48 consecutive launches of
+# k_line_pcr_tile_kernel (all three levels and sweep modes), profiles/k_line_pcr_tile_mix64.md
+NCU_TRAFFIC = {"schur_line_smooth": 1372256.0}
 
 
 def parse_args():
@@ -51,6 +52,23 @@ def parse_args():
     p.add_argument("--batched-streams", type=int, default=16)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (every rank gets it); x itself at world size 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(n_items: int, rank: int, world: int) -> list:
+    """Round-robin share of n_items independent problems for one rank (no exchange)."""
+    return list(range(rank, n_items, world))
 
 
 def dist_setup(args):
@@ -204,11 +222,7 @@ def run_ours(args, world, rank, local):
     ms, res, launches, timing = timed_solves(args.precision, args.steps, args.warmup, groups=[dominant])
     clk = clocks.stop()
     total = sum(ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, world, dev)
     sec = total / 1e3 / args.steps
 
     # 3. end to end through the public API with host buffers (copies inside the timed region)
@@ -255,7 +269,8 @@ def run_ours(args, world, rank, local):
     if not args.no_batched:
         from ot_inputs import batched_problem_specs
 
-        specs = batched_problem_specs(64)
+        specs_all = batched_problem_specs(64)
+        specs = [specs_all[i] for i in shard(len(specs_all), rank, world)]
         bmeshes, items = {}, []
         for n_, K_, a_, b_ in specs:
             if n_ not in bmeshes:
@@ -266,12 +281,13 @@ def run_ours(args, world, rank, local):
         t0 = time.perf_counter()
         bout = capi.ot_ipm_solve_batched(items, options=bopt, n_streams=args.batched_streams, raise_on_error=False)
         torch.cuda.synchronize()
-        tb = time.perf_counter() - t0
+        tb = max_over_ranks(time.perf_counter() - t0, world, dev)
         failed = [i for i, o in enumerate(bout) if o["status"] != 0]
         batched = {"workload": "64 problems, side in {16,24,32,48,64}, K in {8,16,24,32}, 1-4 Gaussians, "
                                "floor 1e-4 (seeds 1000..1063)",
                    "precision": args.precision, "n_streams": args.batched_streams, "seconds": tb,
-                   "problems_per_s": len(items) / tb, "converged": len(items) - len(failed),
+                   "problems_per_s": len(specs_all) / tb, "converged": len(items) - len(failed),
+                   "problems_this_rank": len(items),
                    "failed": {i: capi.STATUS.get(bout[i]["status"], bout[i]["status"]) for i in failed},
                    "newton_steps": sum(o["stats"]["newton_steps"] for o in bout),
                    "unknowns": sum((K_ + 1) * 8 * n_ * n_ + K_ * 2 * n_ * n_ for n_, K_, _, _ in specs)}

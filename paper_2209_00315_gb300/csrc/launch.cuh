@@ -26,19 +26,21 @@ inline dim3 slice_grid(long long n, int S, int threads = 256) {
 // double, with four independent loads in flight per iteration: a block
 // reduces one slice of tens of thousands of values, and a single dependent
 // accumulator would wait for each load in turn.
+// The per-thread partial sums are in T: a block of one slice runs on one SM,
+// where FP64 adds of FP32 data would cost more than the loads.
 template <typename T>
 __device__ __forceinline__ double strided_sum(const T* xs, long long n) {
   const long long b = blockDim.x;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   long long i = threadIdx.x;
   for (; i + 3 * b < n; i += 4 * b) {
-    a0 += (double)xs[i];
-    a1 += (double)xs[i + b];
-    a2 += (double)xs[i + 2 * b];
-    a3 += (double)xs[i + 3 * b];
+    a0 += xs[i];
+    a1 += xs[i + b];
+    a2 += xs[i + 2 * b];
+    a3 += xs[i + 3 * b];
   }
-  for (; i < n; i += b) a0 += (double)xs[i];
-  return (a0 + a1) + (a2 + a3);
+  for (; i < n; i += b) a0 += xs[i];
+  return (double)((a0 + a1) + (a2 + a3));
 }
 
 template <typename... KArgs, typename... Args>

@@ -79,10 +79,14 @@ template struct Hierarchy<float>;
 template struct Hierarchy<double>;
 
 template <typename T>
-void KrylovT<T>::build(int m, i64 n_) {
+void KrylovT<T>::build(int m, i64 n_, bool shadow) {
   release();
   mmax = m;
   n = n_;
+  if (shadow) {
+    V32 = (float*)dev::alloc(sizeof(float) * (size_t)(m + 1) * n);
+    w32 = (float*)dev::alloc(sizeof(float) * (size_t)n);
+  }
   V = (T*)dev::alloc(sizeof(T) * (size_t)(m + 1) * n);
   Z = (T*)dev::alloc(sizeof(T) * (size_t)m * n);
   w = (T*)dev::alloc(sizeof(T) * (size_t)n);
@@ -99,6 +103,9 @@ void KrylovT<T>::release() {
   dev::release(hc1);
   dev::release(hc2);
   dev::release(y);
+  dev::release(V32);
+  dev::release(w32);
+  V32 = w32 = nullptr;
   V = Z = w = nullptr;
   hc1 = hc2 = y = nullptr;
 }
@@ -109,7 +116,7 @@ static double* dalloc(i64 n) { return (double*)dev::alloc(sizeof(double) * (size
 
 int effective_restart(const ot_options& opt, i64 ntot) {
   if (opt.fgmres_restart > 0) return opt.fgmres_restart;
-  const i64 per_vector = 2 * ntot * (i64)sizeof(double);  // one V and one Z vector
+  const i64 per_vector = ntot * (i64)(2 * sizeof(double) + sizeof(float));  // V, Z and the FP32 shadow of V
   const i64 fit = (i64)(dev::krylov_budget() / (size_t)(per_vector > 0 ? per_vector : 1));
   const i64 cap = std::min<i64>(opt.fgmres_max_iter, kMaxRestart);
   return (int)std::max<i64>(std::min<i64>(30, cap), std::min<i64>(cap, fit));
@@ -150,7 +157,7 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
     srhs = dalloc(Nr);
     zeta = dalloc(Nr);
     cur_inner = opt.schur_max_iter;
-    outer.build(cur_restart, ntot);
+    outer.build(cur_restart, ntot, true);
     if (prec == OT_PREC_MIXED) {
       innerf.build(cur_inner, Nr);
       // phi, u, bphi: Np each; rho, s, srhs, zeta, y: Nr each; mean, sums: K+2 each
@@ -346,10 +353,23 @@ static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_a
     T* zj = K.Z + (i64)j * K.n;
     prec(vj, zj);
     op(zj, K.w);
-    k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
+    if constexpr (std::is_same<T, double>::value) {
+      if (K.V32) {
+        // first-pass coefficients in FP32 from the shadow basis: the FP64 second
+        // pass below removes what they leave, so h = h1 + h2 keeps FP64 accuracy
+        k_convert(K.w, K.w32, K.n, 1.0, st);
+        k_mdot(K.V32, K.n, j + 1, K.w32, K.n, K.hc1, W.partial, st);
+      } else {
+        k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
+      }
+    } else {
+      k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
+    }
     k_mupdate(K.V, K.n, j + 1, K.hc1, K.w, K.n, K.hc2, true, false, W.partial, st);
     k_mupdate(K.V, K.n, j + 1, K.hc2, K.w, K.n, K.hc2, false, true, W.partial, st);
     k_scale_by_inv_norm(K.w, K.hc2 + j + 1, K.V + (i64)(j + 1) * K.n, K.n, st);
+    if constexpr (std::is_same<T, double>::value)
+      if (K.V32) k_convert(K.V + (i64)(j + 1) * K.n, K.V32 + (i64)(j + 1) * K.n, K.n, 1.0, st);
     dev::copy_d2h(hb, K.hc1, sizeof(double) * (j + 1), st);
     dev::copy_d2h(hb + W.hoff, K.hc2, sizeof(double) * (j + 2), st);
     dev::sync(st);
@@ -466,6 +486,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   double beta = norm2(W, b, n, st);
   if (beta <= tol_abs) return beta;
   k_scale(b, 1.0 / beta, K.V, n, st);
+  if (K.V32) k_convert(K.V, K.V32, n, 1.0, st);
   OpFn<double> prec = [&](const double* in, double* out) { bb_apply(W, opt, in, out, st); };
   OpFn<double> op = [&](const double* in, double* out) {
     k_kkt_apply(W.d, W.kcoef, in, out, W.xmean, nullptr, st);
@@ -485,6 +506,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
     res = beta;
     if (beta <= tol_abs) break;
     k_scale(K.V, 1.0 / beta, K.V, n, st);
+    if (K.V32) k_convert(K.V, K.V32, n, 1.0, st);
   }
   W.outer_iters += total;
   if (res > tol_abs) W.capped_solves++;

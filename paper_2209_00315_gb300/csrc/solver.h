@@ -36,7 +36,11 @@ struct KrylovT {
   double* hc1 = nullptr;   // mmax+2
   double* hc2 = nullptr;   // mmax+2
   double* y = nullptr;     // mmax
-  void build(int m, i64 n);
+  // FP32 shadow of V and w (shadow = true): the first Gram-Schmidt pass takes
+  // its dot products from them in FP32; the FP64 second pass corrects them.
+  float* V32 = nullptr;    // (mmax+1) x n
+  float* w32 = nullptr;    // n
+  void build(int m, i64 n, bool shadow = false);
   void release();
 };
 typedef KrylovT<double> Krylov;
@@ -95,7 +99,7 @@ constexpr int kMaxRestart = 800;
 
 // FGMRES restart length for these options and ntot unknowns: opt.fgmres_restart
 // if > 0; otherwise (automatic) the iteration cap, i.e. no restart as in the
-// paper, as far as the Krylov basis (2m+1 vectors) fits the thread's budget
+// paper, as far as the Krylov basis (V, Z and V's FP32 shadow) fits the thread's budget
 // (dev::krylov_budget), never below 30.
 int effective_restart(const ot_options& opt, i64 ntot);
 
