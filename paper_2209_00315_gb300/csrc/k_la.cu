@@ -292,7 +292,6 @@ __global__ void __launch_bounds__(256) k_mdot8_kernel(const T* __restrict__ V, i
     const i64 np = n / 2, per = (np + gridDim.x - 1) / gridDim.x;
     const i64 p0 = blockIdx.x * per, p1 = min(np, p0 + per);
     const V2* w2 = reinterpret_cast<const V2*>(w);
-#pragma unroll 2
     for (i64 q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
       const V2 wv = w2[q];
 #pragma unroll
