@@ -242,3 +242,19 @@ def test_full_size_mix64_against_oracle_properties(gpu_lib):
     mass = d.rho_slices(rho) @ d.t.coarse.area
     assert np.abs(mass - d.t.coarse.area @ r0).max() < 1e-12
     assert rho.min() > 0 and s.min() > 0
+
+
+@pytest.mark.parametrize("n,K", [(4, 1), (4, 40), (2, 130)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ipm_matches_oracle_time_slice_extremes(gpu_lib, n, K, precision):
+    """Edge cases of the time dimension: a single density slice (K = 1), two PCR
+    lines per lane (32 < K <= 64: the K-slice line solves span two registers per
+    lane), and K > 128, where the line smoothers fall back to one Thomas sweep
+    per thread and no level is fused."""
+    from ot_inputs import mixture_params
+
+    r0 = make_density(n, *mixture_params(900 + n, 2), 1e-3)
+    r1 = make_density(n, *mixture_params(950 + K, 2), 1e-3)
+    d, res, ref = _ipm_pair(n, K, r0, r1, precision)
+    assert abs(res["cost"] - ref.cost) < 1e-8 * ref.cost
+    assert rel(res["rho"], ref.rho) < 1e-6 and rel(res["phi"], ref.phi) < 1e-6
