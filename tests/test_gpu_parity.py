@@ -258,3 +258,23 @@ def test_ipm_matches_oracle_time_slice_extremes(gpu_lib, n, K, precision):
     d, res, ref = _ipm_pair(n, K, r0, r1, precision)
     assert abs(res["cost"] - ref.cost) < 1e-8 * ref.cost
     assert rel(res["rho"], ref.rho) < 1e-6 and rel(res["phi"], ref.phi) < 1e-6
+
+
+@pytest.mark.parametrize("n,K", [(1, 2), (4, 4), (8, 6)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ipm_matches_oracle_disjoint_supports(gpu_lib, n, K, precision):
+    """Densities with zeros: rho_in lives on the left half, rho_f on the right
+    half (allowed: only rho_in + rho_f > 0 is required); n = 1 is the smallest
+    mesh (two coarse triangles, one multigrid level on the space-time side)."""
+    from ot_inputs import coarse_triangles
+
+    cx = coarse_triangles(n)[:, :, 0].mean(1)
+    d = ipm.discretise(n, K)
+    area = d.t.coarse.area
+    r0 = np.where(cx < 0.5, 1.0, 0.0)
+    r1 = np.where(cx >= 0.5, 1.0, 0.0)
+    r0, r1 = r0 / (area @ r0), r1 / (area @ r1)
+    d, res, ref = _ipm_pair(n, K, r0, r1, precision)
+    assert abs(res["cost"] - ref.cost) < 1e-8 * ref.cost
+    assert rel(res["rho"], ref.rho) < 1e-6 and rel(res["phi"], ref.phi) < 1e-6
+    assert float(res["rho"].min()) > 0
