@@ -269,17 +269,22 @@ static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128
 // into a padded [K][9] shared tile, warp w solves column w by PCR, and the
 // solutions leave through the same tile.
 constexpr int kTileCells = 8;
-template <typename T, int KPL, int MODE>
-__global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+constexpr int kTileThreads = 32 * kTileCells;  // one warp per line of the tile
+
+// The three stages of one tile, run by kTileThreads threads (tid) of a CTA on
+// their own shared tile (3 S (kTileCells+1) values), with a barrier of those
+// threads between stages.  tile: index of the first cell / kTileCells.
+template <typename T, int MODE>
+__device__ __forceinline__ void tile_gather(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color,
+                                            int tile, int tid, T* tsm) {
   constexpr int P = kTileCells + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sd = reinterpret_cast<T*>(smem_raw);  // [S][P] diagonal
-  T* sr = sd + S * P;                      // [S][P] right-hand side, then solution
-  T* st = sr + S * P;                      // [S][P] tau
+  T* sd = tsm;           // [S][P] diagonal
+  T* sr = sd + S * P;    // [S][P] right-hand side, then solution
+  T* st = sr + S * P;    // [S][P] tau
   const int sq = L.m * L.m, ld = (int)L.ld;
-  const int j = threadIdx.x % kTileCells, row0 = threadIdx.x / kTileCells;
-  const int rows = blockDim.x / kTileCells;
-  const int cell = blockIdx.x * kTileCells + j;
+  const int j = tid % kTileCells, row0 = tid / kTileCells;
+  constexpr int rows = kTileThreads / kTileCells;
+  const int cell = tile * kTileCells + j;
   const bool live = cell < sq;
   i64 nb[3] = {-1, -1, -1};
   const int c = color * sq + cell;
@@ -302,33 +307,59 @@ __global__ void __launch_bounds__(256) k_line_pcr_tile_kernel(int S, LevelView<T
     sr[k * P + j] = rhs;
     st[k * P + j] = tau;
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, col = threadIdx.x >> 5;
-  {
-    T a[KPL], d[KPL], cc[KPL], r[KPL];
+}
+
+template <typename T, int KPL>
+__device__ __forceinline__ void tile_solve(int S, int tid, T* tsm) {
+  constexpr int P = kTileCells + 1;
+  T* sd = tsm;
+  T* sr = sd + S * P;
+  T* st = sr + S * P;
+  const int lane = tid & 31, col = tid >> 5;
+  T a[KPL], d[KPL], cc[KPL], r[KPL];
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-      int k = lane + 32 * q;
-      if (k < S) {
-        T tau = st[k * P + col];
-        d[q] = sd[k * P + col];
-        r[q] = sr[k * P + col];
-        a[q] = (k > 0) ? -tau : (T)0;
-        cc[q] = (k < S - 1) ? -tau : (T)0;
-      } else {
-        d[q] = 1; r[q] = 0; a[q] = 0; cc[q] = 0;
-      }
-    }
-    pcr_solve<T, KPL>(a, d, cc, r, lane);
-#pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-      int k = lane + 32 * q;
-      if (k < S) sr[k * P + col] = mg_div(r[q], d[q]);
+  for (int q = 0; q < KPL; ++q) {
+    int k = lane + 32 * q;
+    if (k < S) {
+      T tau = st[k * P + col];
+      d[q] = sd[k * P + col];
+      r[q] = sr[k * P + col];
+      a[q] = (k > 0) ? -tau : (T)0;
+      cc[q] = (k < S - 1) ? -tau : (T)0;
+    } else {
+      d[q] = 1; r[q] = 0; a[q] = 0; cc[q] = 0;
     }
   }
+  pcr_solve<T, KPL>(a, d, cc, r, lane);
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    int k = lane + 32 * q;
+    if (k < S) sr[k * P + col] = mg_div(r[q], d[q]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_store(int S, const LevelView<T>& L, int color, int tile, int tid, const T* tsm) {
+  constexpr int P = kTileCells + 1;
+  const T* sr = tsm + S * P;
+  const int sq = L.m * L.m, ld = (int)L.ld;
+  const int j = tid % kTileCells, row0 = tid / kTileCells;
+  constexpr int rows = kTileThreads / kTileCells;
+  const int cell = tile * kTileCells + j;
+  if (cell < sq)
+    for (int k = row0; k < S; k += rows) L.x[k * ld + color * sq + cell] = sr[k * P + j];
+}
+
+template <typename T, int KPL, int MODE>
+__global__ void __launch_bounds__(kTileThreads) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc,
+                                                                       int color) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tsm = reinterpret_cast<T*>(smem_raw);
+  tile_gather<T, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
   __syncthreads();
-  if (live)
-    for (int k = row0; k < S; k += rows) L.x[k * ld + c] = sr[k * P + j];
+  tile_solve<T, KPL>(S, threadIdx.x, tsm);
+  __syncthreads();
+  tile_store<T>(S, L, color, blockIdx.x, threadIdx.x, tsm);
 }
 
 // Opt a kernel into more than 48 KB of dynamic shared memory (once per size).
@@ -781,9 +812,7 @@ __global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, Le
 // all fused levels in shared memory with odd slice strides; the coarsest level
 // as in k_coarse_kernel.
 template <typename T, int KPL>
-__global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu,
-                                                                                   int nuc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, unsigned char* smem_raw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   __shared__ LevelSet<T> ls;
   stage_levels(gls, ls, reinterpret_cast<T*>(smem_raw), S, S, 0);
@@ -840,6 +869,13 @@ __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kerne
   const LevelView<T>& G0 = gls.L[0];
   const LevelView<T>& V0 = ls.L[0];
   for (SliceWalk w((int)G0.nc); w.k < S; w.next()) G0.x[(i64)w.k * G0.ld + w.c] = V0.x[w.k * (int)V0.ld + w.c];
+}
+
+template <typename T, int KPL>
+__global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu,
+                                                                                   int nuc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sch_lower_body<T, KPL>(S, gls, nu, nuc, smem_raw);
 }
 
 template <typename T>
