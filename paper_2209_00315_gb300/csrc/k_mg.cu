@@ -253,6 +253,68 @@ __device__ __forceinline__ void point_gs_mode(int S, const LevelView<T>& L, cons
   L.x[(i64)k * L.ld + c] = mg_div(num, den);
 }
 
+// Point sweep of one colour laid out by rows of squares: warp w of the CTA
+// takes row J = blockIdx.x * 8 + w, its lanes the squares I of that row, so
+// the cell and its three neighbours follow from (t, I, J) without a division
+// and every load of a row is coalesced.  The same operations in the same
+// order as point_gs / point_gs_mode.
+template <typename T>
+__device__ __forceinline__ int parent_cell(int m, int t, int I, int J) {
+  const int n = m >> 1, a = I & 1, b = J & 1;
+  const int tc = (t == 0) ? ((a == 0 && b == 1) ? 1 : 0) : ((a == 1 && b == 0) ? 0 : 1);
+  return tc * n * n + (J >> 1) * n + (I >> 1);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_point_rows_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  const int m = L.m, mm = m * m, ld = (int)L.ld;
+  const int J = blockIdx.x * 8 + threadIdx.y;
+  if (J >= m) return;
+  const int t = color, to = 1 - color;
+  for (int k = blockIdx.y; k < S; k += gridDim.y) {
+    const T* xs = L.x + k * ld;
+    const T* xcs = (MODE == kSweepAfterProlong) ? Lc.x + k * (int)Lc.ld : nullptr;
+    for (int I = threadIdx.x; I < m; I += 32) {
+      const int c = t * mm + J * m + I;
+      // neighbours (slot 0, 1, 2) as (I, J) of the other triangle type
+      int nI[3], nJ[3];
+      bool has[3];
+      nI[0] = I, nJ[0] = J, has[0] = true;
+      if (t == 0) {
+        nI[1] = I + 1, nJ[1] = J, has[1] = I + 1 < m;
+        nI[2] = I, nJ[2] = J - 1, has[2] = J > 0;
+      } else {
+        nI[1] = I - 1, nJ[1] = J, has[1] = I > 0;
+        nI[2] = I, nJ[2] = J + 1, has[2] = J + 1 < m;
+      }
+      T num = L.b[k * ld + c], den = 0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        T a = L.alpha[(sl * S + k) * ld + c];
+        den += a;
+        if (MODE != kSweepFromZero && has[sl]) {
+          T v = xs[to * mm + nJ[sl] * m + nI[sl]];
+          if (MODE == kSweepAfterProlong) v += xcs[parent_cell<T>(m, to, nI[sl], nJ[sl])];
+          num += a * v;
+        }
+      }
+      L.x[k * ld + c] = mg_div(num, den);
+    }
+  }
+}
+
+// Rows kernel usable: 32-bit indices over the level.
+template <typename T>
+static bool point_rows_ok(int S, const LevelView<T>& L) {
+  return 3 * (i64)S * L.ld < (1ll << 31);
+}
+
+template <typename T, int MODE>
+static void launch_point_rows(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color, Stream st) {
+  const dim3 grid((unsigned)((L.m + 7) / 8), (unsigned)(S < 65535 ? S : 65535));
+  launch(k_point_rows_kernel<T, MODE>, grid, dim3(32, 8), 0, cs(st), S, L, Lc, color);
+}
+
 template <typename T, int KPL>
 __global__ void __launch_bounds__(256) k_line_pcr_kernel(int S, LevelView<T> L, int color) {
   i64 sq = (i64)L.m * L.m;
@@ -405,7 +467,10 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
     else
       launch(k_line_smooth_kernel<T>, nblk(sq), kT, 0, cs(st), S, L, color, line_c, line_r);
   } else {
-    launch(k_point_smooth_kernel<T>, slice_grid(sq, S), kT, 0, cs(st), S, L, color);
+    if (point_rows_ok(S, L))
+      launch_point_rows<T, kSweepPlain>(S, L, L, color, st);
+    else
+      launch(k_point_smooth_kernel<T>, slice_grid(sq, S), kT, 0, cs(st), S, L, color);
   }
   // per updated cell: b, three coefficients, the neighbours' x, the new x (+ tau for lines)
   prof::end(id, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)sq);
@@ -461,9 +526,15 @@ void k_mg_smooth_mode(int S, const LevelView<T>& L, const LevelView<T>* coarse, 
     }
 #undef OT_TILE
   } else if (mode == kSweepFromZero) {
-    launch(k_point_smooth_mode_kernel<T, kSweepFromZero>, slice_grid(sq, S), kT, 0, cs(st), S, L, Lc, color);
+    if (point_rows_ok(S, L))
+      launch_point_rows<T, kSweepFromZero>(S, L, Lc, color, st);
+    else
+      launch(k_point_smooth_mode_kernel<T, kSweepFromZero>, slice_grid(sq, S), kT, 0, cs(st), S, L, Lc, color);
   } else {
-    launch(k_point_smooth_mode_kernel<T, kSweepAfterProlong>, slice_grid(sq, S), kT, 0, cs(st), S, L, Lc, color);
+    if (point_rows_ok(S, L))
+      launch_point_rows<T, kSweepAfterProlong>(S, L, Lc, color, st);
+    else
+      launch(k_point_smooth_mode_kernel<T, kSweepAfterProlong>, slice_grid(sq, S), kT, 0, cs(st), S, L, Lc, color);
   }
   prof::end(id, st, (double)sizeof(T) * (L.tau ? 7.0 : 6.0) * (double)S * (double)sq);
 }
