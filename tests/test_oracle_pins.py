@@ -342,3 +342,38 @@ def test_adjoint_partials_match_finite_differences_of_cost():
               - ipm.cost(d, phi - h * vp, rho - h * vr, r0 - h * v0, r1 - h * v1)) / (2 * h)
         an = dphi @ vp + drho @ vr + d0 @ v0 + d1 @ v1
         assert abs(fd - an) < 1e-7 * max(1.0, abs(fd))
+
+
+@pytest.mark.slow
+def test_separable_densities_converge_to_quantile_w2():
+    """Densities that vary only in x (a narrow and a wide Gaussian profile with a
+    floor, so a dilation as well as a shift): the optimal flow is along x, whose
+    cost on this mesh is 4/3 of the Euclidean one (the walled-strip conductivity
+    3/4), so C -> (4/3) W2^2 / 2 with W2^2 = int_0^1 |F^-1(u) - G^-1(u)|^2 du from
+    the quantile functions of the two profiles (computed here on a fine grid)."""
+    from ot_inputs import _split4, coarse_triangles
+
+    c0, s0, c1, s1, floor = 0.4, 0.08, 0.6, 0.15, 1e-2
+    prof = lambda x, c, s: floor + np.exp(-(x - c) ** 2 / (2 * s * s))  # noqa: E731
+
+    def cell_average(n, c, s):
+        tri = coarse_triangles(n)
+        sub = _split4(_split4(tri))
+        mids = np.stack([(sub[:, 0] + sub[:, 1]) / 2, (sub[:, 1] + sub[:, 2]) / 2, (sub[:, 2] + sub[:, 0]) / 2], 1)
+        v = prof(mids[..., 0], c, s).mean(1).reshape(tri.shape[0], 16).mean(1)
+        return v / (0.5 / (n * n) * v.sum())
+
+    x = np.linspace(0.0, 1.0, 400001)
+    u = (np.arange(200000) + 0.5) / 200000
+
+    def quantile(c, s):
+        f = prof(x, c, s)
+        F = np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(x))])
+        return np.interp(u, F / F[-1], x)
+
+    target = (4.0 / 3.0) * float(np.mean((quantile(c0, s0) - quantile(c1, s1)) ** 2)) / 2.0
+    err = {}
+    for n in (4, 8):
+        d = ipm.discretise(n, n)
+        err[n] = ipm.ipm_solve(d, cell_average(n, c0, s0), cell_average(n, c1, s1)).cost / target - 1.0
+    assert abs(err[8]) < abs(err[4]) < 0.15 and abs(err[8]) < 0.01, err
