@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from .mesh import TriMesh, TwoLevelMesh
 
@@ -214,3 +215,30 @@ def edge_average_plain(m: TriMesh) -> sp.csr_matrix:
     rows = np.concatenate([np.arange(ne), np.arange(ne)])
     cols = np.concatenate([m.edge_cells[:, 0], m.edge_cells[:, 1]])
     return sp.csr_matrix((np.full(2 * ne, 0.5), (rows, cols)), shape=(ne, m.ncell))
+
+
+def bb_apply_exact(d: Discretisation, phi, rho, s, rho0, rho1, v):
+    """One application of the BB block-triangular preconditioner (Sec. 4.3.3,
+    Eq. triang with the Schur block of Eq. pseudoschur-bis) with exact solves:
+
+        z = (Diag(s) A~ - Diag(rho) B M^-1 B~)^-1 (-Diag(rho) d),
+        y = M'^-1 A~ z,
+        b = c - B^T P^T y, with each slice's mean removed (the range of A^j),
+        x^j = the zero-mean solution of A^j x^j = b^j, j = 1..K+1,
+
+    for v = (c; d).  Returns (x, y)."""
+    Np = (d.K + 1) * d.N
+    v = np.asarray(v, dtype=np.float64)
+    c, dv = v[:Np], v[Np:]
+    z = spla.spsolve(d.schur_bb(phi, rho, s).tocsc(), -np.asarray(rho) * dv)
+    y = (d.A_tilde_block(rho) @ z) / np.tile(d.t.coarse.area, d.K)
+    b = (c - d.B_block(phi).T @ (d.P_block().T @ y)).reshape(d.K + 1, d.N)
+    rt = d.rho_tilde(rho, rho0, rho1)
+    x = np.empty_like(b)
+    for j in range(d.K + 1):
+        bj = b[j] - np.mean(b[j])
+        Aj = weighted_laplacian(d.t.fine, rt[j]).tocsc()
+        xj = np.zeros(d.N)
+        xj[1:] = spla.spsolve(Aj[1:, :][:, 1:].tocsc(), bj[1:])   # ground one potential: A^j is singular
+        x[j] = xj - np.mean(xj)
+    return x.ravel(), y

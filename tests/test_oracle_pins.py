@@ -202,6 +202,86 @@ def test_projected_system_reproduces_newton_direction(n, K):
     assert np.allclose(dphi_rec, dphi, atol=1e-9)
 
 
+# ------------------------------------------------- BB preconditioner (Sec. 4.3.3)
+@pytest.mark.parametrize("n,K", [(2, 2), (3, 3), (4, 2)])
+def test_atilde_is_half_the_galerkin_product_of_A(n, K):
+    """With rho constant in time, every A^k uses the edge values R_E rho, and J
+    lifts a coarse function to one that jumps only across fine edges lying on
+    coarse edges.  Each coarse edge holds two fine edges of half its length
+    whose centre distance is also halved (the 4:1 refinement is self-similar),
+    and lambda = 1/2 on both meshes, so J^T A^k J = 2 A~^k exactly."""
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(10 * n + K)
+    rc = rng.uniform(0.5, 2, d.Nc)
+    A = d.A_block(np.tile(rc, K), rc, rc)
+    JJ = d.J_block(K + 1)
+    G = (JJ.T @ A @ JJ).toarray()
+    At = d.A_tilde_block(np.tile(rc, K)).toarray()
+    Nc = d.Nc
+    for k in range(K):
+        blk = slice(k * Nc, (k + 1) * Nc)
+        assert np.abs(0.5 * G[blk, blk] - At[blk, blk]).max() < 1e-13 * np.abs(At).max()
+
+
+@pytest.mark.parametrize("n,K", [(2, 2), (3, 3)])
+def test_btilde_is_the_block_transpose_of_B_on_coarse_functions(n, K):
+    """Reading R5 with R_T = R_E^T diag(|w||e|) and lambda = 1/2 gives
+    J^T R_f^T W = R_T, so on coarse functions B~ carries the same transport
+    term (grad phi^j . grad, averaged over the two density slices next to
+    phi^j) as B, on the swapped time staggering: block (j, k) of J^T B~ equals
+    block (k, j) of B J except for the time differences, which enter the two
+    with opposite signs, (J^T B~)_{jk} - (B J)_{kj} = (2/dt) M' (d_jk - d_{j,k+1})."""
+    d = ipm.discretise(n, K)
+    phi = np.random.default_rng(n + K).standard_normal((K + 1) * d.N)
+    JJ = d.J_block(K + 1)
+    L = (JJ.T @ d.B_tilde_block(phi)).toarray()
+    R = (d.B_block(phi) @ JJ).toarray()
+    Nc, Mp = d.Nc, d.Mc.toarray()
+    scale = np.abs(L).max()
+    for j in range(K + 1):
+        for k in range(K):
+            diff = L[j * Nc:(j + 1) * Nc, k * Nc:(k + 1) * Nc] - R[k * Nc:(k + 1) * Nc, j * Nc:(j + 1) * Nc]
+            want = (2.0 / d.dt) * Mp * (float(j == k) - float(j == k + 1))
+            assert np.abs(diff - want).max() < 1e-13 * scale
+
+
+@pytest.mark.parametrize("n,K", [(2, 2), (3, 3)])
+def test_exact_bb_application_solves_its_triangular_factor(n, K):
+    """With exact inner solves the BB application returns (x, y) with
+      * y the solution of the approximated Schur system of Eq. (schur-linear-system),
+        P (C - B M^-1 B~ A~^+ M') P^T y = -d for d in the range of P, built here
+        with a dense pseudo-inverse instead of the rescaled system (pseudoschur-bis)
+        and y = M'^-1 A~ z that the application uses;
+      * y in the range of P^T, as Sec. 4.3.3 requires of the solution;
+      * x from the first block row of the projected system, A x = c - B^T P^T y
+        up to per-slice constants (the range of A), with zero slice means."""
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(40 + n + K)
+    r0 = rng.uniform(0.5, 2, d.Nc)
+    r1 = rng.uniform(0.5, 2, d.Nc)
+    r1 *= (d.t.coarse.area @ r0) / (d.t.coarse.area @ r1)
+    phi = 0.3 * rng.standard_normal((K + 1) * d.N)
+    rho = ipm.renormalise(d, rng.uniform(0.5, 2, K * d.Nc), r0)
+    s = rng.uniform(0.5, 2, K * d.Nc)
+    Np, Nr = (K + 1) * d.N, K * d.Nc
+    P = d.P_block().toarray()
+    c = rng.standard_normal(Np)
+    dv = P @ rng.standard_normal(Nr)
+    x, y = ops.bb_apply_exact(d, phi, rho, s, r0, r1, np.concatenate([c, dv]))
+    Mp = d.Mc_block().toarray()
+    Minv = np.diag(1.0 / np.tile(d.t.fine.area, K + 1))
+    B = d.B_block(phi).toarray()
+    St = P @ (d.C_block(rho, s).toarray()
+              - B @ Minv @ d.B_tilde_block(phi).toarray() @ np.linalg.pinv(d.A_tilde_block(rho).toarray()) @ Mp) @ P.T
+    assert np.abs(St @ y + dv).max() < 1e-9 * np.abs(dv).max()
+    # y = M'^-1 A~ z has zero mass per slice (A~ has zero column sums), so P^T y = y
+    assert np.abs(P.T @ y - y).max() < 1e-12 * np.abs(y).max()
+    Kp = d.projected_kkt(phi, rho, s, r0, r1).toarray()
+    r = (Kp[:Np] @ np.concatenate([x, y]) - c).reshape(K + 1, d.N)
+    assert np.abs(r - r.mean(axis=1, keepdims=True)).max() < 1e-10 * np.abs(c).max()
+    assert np.abs(x.reshape(K + 1, d.N).mean(axis=1)).max() < 1e-12 * np.abs(x).max()
+
+
 # ------------------------------------------------------------------- IPM
 def test_uniform_densities_exact_solution():
     """rho_in = rho_f = c: rho^k = c, s = mu/c, phi^k = -(k-1) dt mu/c + const, C = 0, one Newton step per stage."""
