@@ -12,7 +12,7 @@ code with the CUDA library: the two only share the seeded input generators of
 Modules
   mesh       generic triangle meshes, the midpoint 4-split, TPFA geometry (Sec. 2.1)
   operators  sparse matrices of Sec. 2.1-3 and of the projected / BB systems (Sec. 4.3),
-             and one BB application with exact inner solves
+             and one BB or SIMPLE application with exact inner solves
   ipm        residual F, Jacobian, exact Newton directions, the IPM loop, cost and dual value
   adjoint    gradient of the cost with respect to rho_in, rho_f (transposed-Jacobian solve)
 

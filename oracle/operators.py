@@ -242,3 +242,29 @@ def bb_apply_exact(d: Discretisation, phi, rho, s, rho0, rho1, v):
         xj[1:] = spla.spsolve(Aj[1:, :][:, 1:].tocsc(), bj[1:])   # ground one potential: A^j is singular
         x[j] = xj - np.mean(xj)
     return x.ravel(), y
+
+
+def simple_apply_exact(d: Discretisation, phi, rho, s, rho0, rho1, v):
+    """One application of the SIMPLE preconditioner (Sec. 4.2) to the projected
+    system (B -> P B, C -> P C P^T), with A^ = Diag(A) and an exact solve of
+    S^ = -(P C P^T + P B A^-1 B^T P^T):
+
+        x1 = A^-1 c,   y = S^-1 (d - P B x1),   x = x1 - A^-1 B^T P^T y,
+
+    the product of the three block factors applied to v = (c; d).  S^ is block
+    tridiagonal in time and vanishes on per-slice constants; d - P B x1 has zero
+    slice sums (it lies in the range of P), and y is the solution with
+    |c'|^T y^k = 0 (the range of P^T), found from the system bordered by those
+    K constraints.  Returns (x, y)."""
+    Np = (d.K + 1) * d.N
+    v = np.asarray(v, dtype=np.float64)
+    c, dv = v[:Np], v[Np:]
+    Ad = d.A_block(rho, rho0, rho1).diagonal()
+    P = d.P_block()
+    Bp = (P @ d.B_block(phi)).tocsr()
+    S = -(P @ d.C_block(rho, s) @ P.T + Bp @ sp.diags(1.0 / Ad) @ Bp.T)
+    Y = sp.kron(sp.identity(d.K), sp.csr_matrix(d.t.coarse.area[:, None]))
+    bordered = sp.bmat([[S, Y], [Y.T, None]]).tocsc()
+    x1 = c / Ad
+    y = spla.spsolve(bordered, np.concatenate([dv - Bp @ x1, np.zeros(d.K)]))[:d.K * d.Nc]
+    return x1 - (Bp.T @ y) / Ad, y

@@ -282,6 +282,100 @@ def test_exact_bb_application_solves_its_triangular_factor(n, K):
     assert np.abs(x.reshape(K + 1, d.N).mean(axis=1)).max() < 1e-12 * np.abs(x).max()
 
 
+@pytest.mark.parametrize("n,K", [(2, 2), (3, 3)])
+def test_simple_application_inverts_its_block_approximation(n, K):
+    """The three SIMPLE factors (Sec. 4.2) multiply to the inverse of the projected
+    system with A replaced by Diag(A): u = (x, y) solves
+    [Diag(A), B^T P^T; P B, -P C P^T] u = (c; d) for d in the range of P,
+    checked against that matrix assembled from the projected system's blocks."""
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(60 + n + K)
+    r0 = rng.uniform(0.5, 2, d.Nc)
+    r1 = rng.uniform(0.5, 2, d.Nc)
+    r1 *= (d.t.coarse.area @ r0) / (d.t.coarse.area @ r1)
+    phi = 0.3 * rng.standard_normal((K + 1) * d.N)
+    rho = ipm.renormalise(d, rng.uniform(0.5, 2, K * d.Nc), r0)
+    s = rng.uniform(0.5, 2, K * d.Nc)
+    Np = (K + 1) * d.N
+    P = d.P_block()
+    c = rng.standard_normal(Np)
+    dv = P @ rng.standard_normal(K * d.Nc)
+    x, y = ops.simple_apply_exact(d, phi, rho, s, r0, r1, np.concatenate([c, dv]))
+    Kp = d.projected_kkt(phi, rho, s, r0, r1).toarray()
+    Kp[:Np, :Np] = np.diag(np.diag(Kp[:Np, :Np]))
+    r = Kp @ np.concatenate([x, y]) - np.concatenate([c, dv])
+    assert np.abs(r).max() < 1e-10 * max(np.abs(c).max(), np.abs(dv).max())
+    assert np.abs(P.T @ y - y).max() < 1e-12 * np.abs(y).max()
+
+
+def _gmres_right(apply_op, b, apply_prec, tol=1e-5, maxit=300):
+    """Iterations of right-preconditioned GMRES (dense, two Gram-Schmidt passes) to ||r|| <= tol ||b||."""
+    beta = np.linalg.norm(b)
+    V = np.zeros((maxit + 1, b.size))
+    H = np.zeros((maxit + 1, maxit))
+    V[0] = b / beta
+    for j in range(maxit):
+        w = apply_op(apply_prec(V[j]))
+        for _ in range(2):
+            h = V[:j + 1] @ w
+            w = w - h @ V[:j + 1]
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        e1 = np.zeros(j + 2)
+        e1[0] = beta
+        yk = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+        if np.linalg.norm(H[:j + 2, :j + 1] @ yk - e1) <= tol * beta or H[j + 1, j] < 1e-14 * beta:
+            return j + 1
+        V[j + 1] = w / H[j + 1, j]
+    return maxit
+
+
+@pytest.mark.slow
+def test_preconditioner_iteration_trends_along_the_barrier_path():
+    """Sec. 4.2-4.3 and the summary of Sec. 4.4, with exact inner solves: at the
+    first Newton step of each mu stage (4x4 squares, K = 4, the 3-Gaussian
+    mixtures of seeds 2 and 3, floor 1e-4), the BB-preconditioned GMRES needs
+    more iterations as mu decreases, while SIMPLE needs fewer over the late
+    stages and more than BB at mu = 1 (measured: BB 4 -> 18, SIMPLE 56 -> 26)."""
+    from ot_inputs import mixture_params
+
+    n, K = 4, 4
+    d = ipm.discretise(n, K)
+    r0 = make_density(n, *mixture_params(2, 3), 1e-4)
+    r1 = make_density(n, *mixture_params(3, 3), 1e-4)
+    opt = ipm.IPMOptions()
+    phi, rho, s = ipm.initial_point(d, r0, r1, opt.mu0)
+    mu = opt.mu0
+    Np = (K + 1) * d.N
+    bb_its, simple_its = [], []
+    for _ in range(ipm.stage_count(K, opt, d.area_total)):
+        F = ipm.residual(d, phi, rho, s, r0, r1, mu)
+        f0 = fn = ipm.residual_norm(F)
+        first = True
+        while fn > opt.newton_tol * max(1.0, f0):
+            if first:
+                Kp = d.projected_kkt(phi, rho, s, r0, r1)
+                gt = -F[1] + np.tile(d.t.coarse.area, K) * F[2] / rho
+                b = np.concatenate([-F[0], d.P_block() @ gt])
+                state = (phi, rho, s, r0, r1)
+                bb_its.append(_gmres_right(lambda x: Kp @ x, b,
+                                           lambda v: np.concatenate(ops.bb_apply_exact(d, *state, v))))
+                simple_its.append(_gmres_right(lambda x: Kp @ x, b,
+                                               lambda v: np.concatenate(ops.simple_apply_exact(d, *state, v))))
+                first = False
+            dphi, drho, ds, _ = ipm.newton_direction(d, phi, rho, s, r0, r1, mu)
+            a = min(ipm.step_length(rho, drho, opt.tau), ipm.step_length(s, ds, opt.tau))
+            phi, rho, s = phi + a * dphi, ipm.renormalise(d, rho + a * drho, r0), s + a * ds
+            F = ipm.residual(d, phi, rho, s, r0, r1, mu)
+            fn = ipm.residual_norm(F)
+        mu *= opt.mu_factor
+    assert len(bb_its) == 10
+    assert all(b1 <= b2 for b1, b2 in zip(bb_its, bb_its[1:])) and bb_its[-1] >= 3 * bb_its[0]
+    peak = int(np.argmax(simple_its))
+    assert peak <= 2 and all(a >= b for a, b in zip(simple_its[peak:], simple_its[peak + 1:]))
+    assert simple_its[-1] < 0.6 * simple_its[peak] and simple_its[0] > 5 * bb_its[0]
+
+
 # ------------------------------------------------------------------- IPM
 def test_uniform_densities_exact_solution():
     """rho_in = rho_f = c: rho^k = c, s = mu/c, phi^k = -(k-1) dt mu/c + const, C = 0, one Newton step per stage."""
