@@ -337,11 +337,13 @@ using OpFn = std::function<void(const T*, T*)>;
 
 // One restart cycle of right-preconditioned flexible GMRES.  K.V[0] holds the
 // normalised residual, beta its norm.  Classical Gram-Schmidt with one
-// reorthogonalisation on the device; Givens rotations on the host.  On return
-// x += Z y and *res is the residual estimate; returns the number of steps.
+// reorthogonalisation on the device; Givens rotations on the host.  With an
+// FP32 shadow of the basis the first pass takes its coefficients from it, and
+// so does the second when fp32_reorth is set.  On return x += Z y and *res is
+// the residual estimate; returns the number of steps.
 template <typename T>
 static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_abs, const OpFn<T>& prec,
-                   const OpFn<T>& op, T* x, double* res, Stream st) {
+                   const OpFn<T>& op, T* x, double* res, Stream st, bool fp32_reorth = false) {
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 1.0), sn(m, 0.0), g(m + 1, 0.0);
   auto h = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
   g[0] = beta;
@@ -353,19 +355,32 @@ static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_a
     T* zj = K.Z + (i64)j * K.n;
     prec(vj, zj);
     op(zj, K.w);
+    // Coefficients are always applied to w in FP64 and H records exactly the
+    // ones applied, so the Arnoldi relation A Z = V H holds to FP64 rounding
+    // whichever precision computed them.  First pass from the FP32 shadow; the
+    // second pass removes what its rounding left.  Second-pass coefficients
+    // from the shadow too limit the orthogonality of V to ~1e-7, which moves
+    // the residual estimate by that relative amount: harmless for a target of
+    // 1e-5, so fgmres() asks for it only when the target is >= 1e-8.
+    bool shadow_passes = false;
     if constexpr (std::is_same<T, double>::value) {
       if (K.V32) {
-        // first-pass coefficients in FP32 from the shadow basis: the FP64 second
-        // pass below removes what they leave, so h = h1 + h2 keeps FP64 accuracy
+        shadow_passes = true;
         k_convert(K.w, K.w32, K.n, 1.0, st);
         k_mdot(K.V32, K.n, j + 1, K.w32, K.n, K.hc1, W.partial, st);
-      } else {
-        k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
+        if (fp32_reorth) {
+          k_mupdate(K.V, K.n, j + 1, K.hc1, K.w, K.n, K.hc2, false, false, W.partial, st);
+          k_convert(K.w, K.w32, K.n, 1.0, st);
+          k_mdot(K.V32, K.n, j + 1, K.w32, K.n, K.hc2, W.partial, st);
+        } else {
+          k_mupdate(K.V, K.n, j + 1, K.hc1, K.w, K.n, K.hc2, true, false, W.partial, st);
+        }
       }
-    } else {
-      k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
     }
-    k_mupdate(K.V, K.n, j + 1, K.hc1, K.w, K.n, K.hc2, true, false, W.partial, st);
+    if (!shadow_passes) {
+      k_mdot(K.V, K.n, j + 1, K.w, K.n, K.hc1, W.partial, st);
+      k_mupdate(K.V, K.n, j + 1, K.hc1, K.w, K.n, K.hc2, true, false, W.partial, st);
+    }
     k_mupdate(K.V, K.n, j + 1, K.hc2, K.w, K.n, K.hc2, false, true, W.partial, st);
     k_scale_by_inv_norm(K.w, K.hc2 + j + 1, K.V + (i64)(j + 1) * K.n, K.n, st);
     if constexpr (std::is_same<T, double>::value)
@@ -487,6 +502,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   if (beta <= tol_abs) return beta;
   k_scale(b, 1.0 / beta, K.V, n, st);
   if (K.V32) k_convert(K.V, K.V32, n, 1.0, st);
+  const bool fp32_reorth = tol_abs >= 1e-8 * beta;
   OpFn<double> prec = [&](const double* in, double* out) { bb_apply(W, opt, in, out, st); };
   OpFn<double> op = [&](const double* in, double* out) {
     k_kkt_apply(W.d, W.kcoef, in, out, W.xmean, nullptr, st);
@@ -496,7 +512,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   while (true) {
     int m = std::min(std::min(effective_restart(opt, n), K.mmax), opt.fgmres_max_iter - total);
     if (m <= 0) break;
-    total += arnoldi(W, K, m, beta, tol_abs, prec, op, x, &res, st);
+    total += arnoldi(W, K, m, beta, tol_abs, prec, op, x, &res, st, fp32_reorth);
     if (res <= tol_abs || total >= opt.fgmres_max_iter) break;
     // restart from the true residual
     op(x, K.w);

@@ -36,8 +36,9 @@ struct KrylovT {
   double* hc1 = nullptr;   // mmax+2
   double* hc2 = nullptr;   // mmax+2
   double* y = nullptr;     // mmax
-  // FP32 shadow of V and w (shadow = true): the first Gram-Schmidt pass takes
-  // its dot products from them in FP32; the FP64 second pass corrects them.
+  // FP32 shadow of V and w (shadow = true): the Gram-Schmidt dot products are
+  // taken from them in FP32 (the first pass always, the second when the solve's
+  // target allows); the coefficients are applied to the FP64 basis.
   float* V32 = nullptr;    // (mmax+1) x n
   float* w32 = nullptr;    // n
   void build(int m, i64 n, bool shadow = false);
