@@ -104,24 +104,33 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
-            except ValueError:
-                continue
+        with open(self.path) as fh:
+            lines = fh.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
-        pmax = max(r[2] for r in rows)
-        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[3][i].lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows), "power_w_max": pmax}
+        return summarise_clocks(lines)
+
+
+def summarise_clocks(lines) -> dict | None:
+    """Summary of nvidia-smi samples in the QUERY order (csv, no header, no units):
+    median SM clock over the samples drawing at least half the peak power (the
+    timed work), the maximum SM clock, and every throttle reason seen Active."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    pmax = max(r[2] for r in rows)
+    load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[3][i].lower() == "active"})
+    return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows), "power_w_max": pmax}
 
 
 # ------------------------------------------------------------------ CPU oracle
