@@ -71,7 +71,9 @@ typedef enum { OT_PREC_FP64 = 0, OT_PREC_MIXED = 1 } ot_precision;
 /* Solver options; ot_default_options() fills the values used by the paper. */
 typedef struct {
   int32_t memspace;         /* OT_MEM_DEVICE or OT_MEM_HOST */
-  int32_t precision;        /* OT_PREC_FP64: everything FP64; OT_PREC_MIXED: the BB preconditioner in FP32 */
+  int32_t precision;        /* OT_PREC_FP64: FP64 arithmetic, except that the outer FGMRES takes its
+                               Gram-Schmidt coefficients from an FP32 copy of the basis (applied in
+                               FP64); OT_PREC_MIXED: also the BB preconditioner in FP32 */
   double mu_factor;         /* mu_{l+1} = mu_factor mu_l (0.2) */
   double tau;               /* fraction to the boundary (0.99) */
   double newton_tol;        /* Newton stop: ||F|| <= newton_tol max(1, ||F_stage_start||) (1e-6) */
