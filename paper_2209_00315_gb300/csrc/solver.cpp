@@ -355,13 +355,13 @@ static int arnoldi(Workspace& W, KrylovT<T>& K, int m, double beta, double tol_a
     T* zj = K.Z + (i64)j * K.n;
     prec(vj, zj);
     op(zj, K.w);
-    // Coefficients are always applied to w in FP64 and H records exactly the
-    // ones applied, so the Arnoldi relation A Z = V H holds to FP64 rounding
-    // whichever precision computed them.  First pass from the FP32 shadow; the
-    // second pass removes what its rounding left.  Second-pass coefficients
-    // from the shadow too limit the orthogonality of V to ~1e-7, which moves
-    // the residual estimate by that relative amount: harmless for a target of
-    // 1e-5, so fgmres() asks for it only when the target is >= 1e-8.
+    // With an FP64 basis the coefficients are applied to w in FP64 and H records
+    // exactly the ones applied, so the Arnoldi relation A Z = V H holds to FP64
+    // rounding whichever precision computed them.  First pass from the FP32
+    // shadow; the second pass removes what its rounding left.  Second-pass
+    // coefficients from the shadow too limit the orthogonality of V to ~1e-7,
+    // which moves the residual estimate by that relative amount: harmless for a
+    // target of 1e-5, so fgmres() asks for it only when the target is >= 1e-8.
     bool shadow_passes = false;
     if constexpr (std::is_same<T, double>::value) {
       if (K.V32) {
