@@ -34,6 +34,16 @@ WORKLOAD_DESC = ("64x64 squares -> 8192 coarse / 32768 fine triangles, K=32, 3-G
 SAMPLE_N, SAMPLE_K = 12, 6   # bounded sample of the same density recipe for the CPU oracle
 SAMPLE_EVERY = 16            # time one launch in 16 of the roofline kernel inside the timed region
 METRIC = "IPM time-to-solution at duality gap 1e-6"
+WORKLOAD_N, WORKLOAD_K = 64, 32
+
+
+def workload_config(args, world: int) -> dict:
+    """The config object both arms print (the reference arm times a bounded sample of this
+    workload and names the sample in its cpu_baseline)."""
+    n, K = WORKLOAD_N, WORKLOAD_K
+    return {"workload": WORKLOAD_DESC, "precision": args.precision, "n": n, "K": K,
+            "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+            "unknowns": (K + 1) * 8 * n * n + K * 2 * n * n}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in profiles/ (None if the
 # kernel changed since it was taken): schur_line_smooth = mean over 48 consecutive launches of
 # k_line_pcr_tile_kernel (all three levels and sweep modes), profiles/k_line_pcr_tile_mix64.md
@@ -162,7 +172,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{SAMPLE_N}x{SAMPLE_N} squares, K={SAMPLE_K} sample of: {WORKLOAD_DESC}"},
+            "config": workload_config(args, world),
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -182,6 +192,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     n, K, r0, r1 = config_densities(WORKLOAD)
+    assert (n, K) == (WORKLOAD_N, WORKLOAD_K)
     mesh = capi.Mesh(n)
     r0d = torch.from_numpy(r0).to(dev)
     r1d = torch.from_numpy(r1).to(dev)
@@ -311,13 +322,11 @@ def run_ours(args, world, rank, local):
         return
     st = res["stats"]
     line = {
-        "metric": f"{METRIC} ({'mixed FP32-multigrid' if args.precision == 'mixed' else 'FP64'} GPU path)",
+        "metric": METRIC,
         "value": sec, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "n": n, "K": K,
-                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
-                   "unknowns": Np + Nr},
+        "config": workload_config(args, world),
         "solves_per_s": world * args.steps / (total / 1e3),
         "newton_solves_per_s": world * st["newton_steps"] / sec,
         "result": {"cost": res["cost"], "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"],
