@@ -105,6 +105,28 @@ def test_operator_identities():
     assert np.allclose(d.RE @ np.ones(d.Nc), 1.0)
 
 
+def test_operator_identities_on_a_graded_mesh():
+    """The same identities where the coarse cells differ in area (the grid stretched
+    along x), which tells P = I - M' E'^T E'/|Omega| from its transpose: P kills
+    the per-slice mass vectors M'E'^T, P^T y has zero mass in every slice, P^2 = P,
+    and J^T M J = M' for any midpoint 4-split."""
+    xy, tri = mesh.square_grid(3)
+    xy = xy.copy()
+    xy[:, 0] += 0.15 * xy[:, 0] * (1.0 - xy[:, 0])
+    fxy, ftri, parent = mesh.refine4(xy, tri)
+    t = mesh.TwoLevelMesh(mesh.build_mesh(xy, tri), mesh.build_mesh(fxy, ftri), parent, 3)
+    d = ops.Discretisation(t, 2)
+    area = t.coarse.area
+    assert area.max() - area.min() > 0.01
+    P = d.P_block().toarray()
+    mcE = np.kron(np.eye(d.K), area[:, None])
+    assert np.abs(P @ mcE).max() < 1e-15 and np.abs(P @ P - P).max() < 1e-14
+    y = np.random.default_rng(4).standard_normal(d.K * d.Nc)
+    assert np.abs((P.T @ y).reshape(d.K, d.Nc) @ area).max() < 1e-15
+    assert np.allclose((d.J.T @ d.M @ d.J).toarray(), d.Mc.toarray(), atol=1e-16)
+    assert abs(d.area_total - 1.0) < 1e-14
+
+
 # ----------------------------------------------------------------- Jacobian
 def _random_state(d, seed=0):
     rng = np.random.default_rng(seed)
