@@ -87,6 +87,30 @@ def test_schur_operator_matches_oracle(cases):
         assert rel(out, S @ z) < 1e-13, (n, K)
 
 
+@pytest.mark.parametrize("n,K", [(2, 2), (4, 3)])
+def test_bb_application_matches_exact_oracle(gpu_lib, n, K):
+    """One application of the BB preconditioner (Sec. 4.3.3) in FP64 with the inner
+    Schur GMRES driven to 1e-13 and 60 V-cycles per slice Laplacian, against the
+    oracle's application with sparse-LU solves.  x is compared after removing each
+    slice's mean, the constant that the singular slice Laplacians leave free."""
+    from paper_2209_00315_gb300 import capi
+    from oracle import operators as ops
+
+    d = ipm.discretise(n, K)
+    phi, rho, s, r0, r1 = random_state(d, 7 * n + K)
+    phi = 0.1 * phi
+    Np = (K + 1) * d.N
+    v = np.random.default_rng(5).standard_normal(Np + K * d.Nc)
+    x, y = ops.bb_apply_exact(d, phi, rho, s, r0, r1, v)
+    opt = capi.default_options(precision="fp64", eps_schur=1e-13, schur_max_iter=400, lap_cycles=60)
+    out = capi.ot_bb_apply(capi.Mesh(n), K, T(phi), T(rho), T(s), T(r0), T(r1), T(v), options=opt)
+    out = out.cpu().numpy()
+    gx = out[:Np].reshape(K + 1, d.N)
+    gx = (gx - gx.mean(axis=1, keepdims=True)).ravel()
+    assert rel(gx, x) < 1e-10, (n, K)
+    assert rel(out[Np:], y) < 1e-10, (n, K)
+
+
 def test_cost_and_dual_match_oracle(cases):
     from paper_2209_00315_gb300 import capi
 
