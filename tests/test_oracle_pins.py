@@ -398,6 +398,58 @@ def test_preconditioner_iteration_trends_along_the_barrier_path():
     assert simple_its[-1] < 0.6 * simple_its[peak] and simple_its[0] > 5 * bb_its[0]
 
 
+# ----------------------------------------------------------------- symmetries
+def _image(points, mapped):
+    """Index j with points[j] == mapped[i] for every i (a permutation, else AssertionError)."""
+    dist = np.linalg.norm(points[None, :, :] - mapped[:, None, :], axis=2)
+    j = dist.argmin(axis=1)
+    assert dist[np.arange(len(j)), j].max() < 1e-12 and len(set(j.tolist())) == len(j)
+    return j
+
+
+def test_solution_respects_time_reversal_and_mesh_symmetries():
+    """The barrier problem is strictly convex in rho (Sec. 3), so its solution inherits
+    every symmetry of the data.  Swapping rho_in and rho_f reverses time: rho^k and s^k
+    go to slice K+1-k, phi^k to -phi^(K+2-k), the cost is unchanged.  The grid of squares
+    cut along their (0,0)->(1,1) diagonals is invariant under the point reflection
+    (x, y) -> (1-x, 1-y) and the swap (x, y) -> (y, x), which permute the cells.  Random
+    (not symmetric) densities, so any term that treats the two time ends, the two cells
+    of an edge or the two axes differently shows up."""
+    n, K = 3, 3
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(11)
+    area = d.t.coarse.area
+    r0, r1 = rng.uniform(0.2, 2.0, d.Nc), rng.uniform(0.2, 2.0, d.Nc)
+    r0, r1 = r0 / (area @ r0), r1 / (area @ r1)
+    opt = ipm.IPMOptions(gap_tol=1e-3, final_newton_tol=1e-12)
+
+    def solve(a, b):
+        res = ipm.ipm_solve(d, a, b, opt)
+        return (res.rho.reshape(K, d.Nc), res.s.reshape(K, d.Nc),
+                ipm.phi_gauge(d, res.phi).reshape(K + 1, d.N), res.cost)
+
+    rho, s, phi, c = solve(r0, r1)
+    scale = np.abs(phi).max()
+    # time reversal
+    rho2, s2, phi2, c2 = solve(r1, r0)
+    assert abs(c2 - c) < 1e-10 * c
+    assert np.abs(rho2 - rho[::-1]).max() < 1e-9 * rho.max()
+    assert np.abs(s2 - s[::-1]).max() < 1e-9 * s.max()
+    assert np.abs(phi2 + phi[::-1]).max() < 1e-9 * scale
+    # mesh symmetries
+    for f in (lambda p: 1.0 - p, lambda p: p[:, ::-1]):
+        pc = _image(d.t.coarse.bary, f(d.t.coarse.bary))
+        pf = _image(d.t.fine.bary, f(d.t.fine.bary))
+        assert np.allclose(area[pc], area) and np.allclose(d.t.fine.area[pf], d.t.fine.area)
+        rho3, s3, phi3, c3 = solve(r0[pc], r1[pc])
+        assert abs(c3 - c) < 1e-10 * c
+        assert np.abs(rho3 - rho[:, pc]).max() < 1e-9 * rho.max()
+        assert np.abs(s3 - s[:, pc]).max() < 1e-9 * s.max()
+        assert np.abs(phi3 - phi[:, pf]).max() < 1e-9 * scale
+    # the data are not symmetric themselves
+    assert np.abs(r0[pc] - r0).max() > 0.1 and np.abs(r1 - r0).max() > 0.1
+
+
 # ------------------------------------------------------------------- IPM
 def test_uniform_densities_exact_solution():
     """rho_in = rho_f = c: rho^k = c, s = mu/c, phi^k = -(k-1) dt mu/c + const, C = 0, one Newton step per stage."""
