@@ -26,6 +26,7 @@ def main(argv=None):
     p.add_argument("--verbose", action="store_true", help="print one line per barrier stage")
     p.add_argument("--restart", type=int, default=None, help="FGMRES restart length")
     p.add_argument("--max-iter", type=int, default=None, help="FGMRES iteration cap per Newton step")
+    p.add_argument("--mu-factor", type=float, default=None, help="barrier reduction per stage (default 0.2)")
     a = p.parse_args(argv)
 
     from ot_inputs import config_densities
@@ -39,6 +40,8 @@ def main(argv=None):
         extra["fgmres_restart"] = a.restart
     if a.max_iter is not None:
         extra["fgmres_max_iter"] = a.max_iter
+    if a.mu_factor is not None:
+        extra["mu_factor"] = a.mu_factor
     opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
     walls, res = [], None
     for _ in range(a.repeat):
@@ -53,6 +56,7 @@ def main(argv=None):
         "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"], "inner_iters": st["inner_iters"],
         "gap": st["gap"], "wall_s": walls, "kernel_launches": capi.ot_kernel_launches(),
         "fgmres_restart": opt.fgmres_restart, "fgmres_max_iter": opt.fgmres_max_iter,
+        "mu_factor": opt.mu_factor, "mu_final": st["mu"],
     }))
 
 
