@@ -31,6 +31,12 @@ def test_mesh_counts_and_nesting(n):
     assert np.all(counts == 4)
     child_area = np.bincount(t.parent, weights=t.fine.area)
     assert np.allclose(child_area, t.coarse.area, rtol=0, atol=1e-15)
+    # J: every fine cell lies inside its parent (positive barycentric coordinates of its centroid)
+    a, b, c = (t.coarse.xy[t.coarse.tri[t.parent, i]] for i in range(3))
+    g = t.fine.bary
+    cross = lambda u, v: u[:, 0] * v[:, 1] - u[:, 1] * v[:, 0]  # noqa: E731
+    lam = np.stack([cross(b - g, c - g), cross(c - g, a - g), cross(a - g, b - g)], 1)
+    assert np.all(lam > 0.05 * np.abs(lam).sum(1, keepdims=True))
 
 
 @pytest.mark.parametrize("n", [2, 4])
