@@ -1,0 +1,101 @@
+"""Planted mistakes in the oracle, each of which some pin must catch.
+
+Every case copies oracle/, ot_inputs/ and the pin tests into a temporary
+directory, plants one plausible mistake in the copy (a dropped factor, a wrong
+sign or time index, a transposed operand, a wrong parent cell) and runs the pins
+named for it there, in a child process: at least one must fail.  The
+repository's own files are never modified.  A control run of the unchanged copy
+passes the same pins.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (file under oracle/, text, replacement, pins (-k expression) that must catch it)
+MUTATIONS = {
+    "gradient divides by |e| instead of |w|": (
+        "operators.py", "sp.diags(1.0 / m.edge_dist) @ incidence(m).T", "sp.diags(1.0 / m.edge_len) @ incidence(m).T",
+        "conductivity"),
+    "projector P exchanged for its transpose": (
+        "operators.py", "np.outer(mc, np.ones(self.Nc))", "np.outer(np.ones(self.Nc), mc)", "graded"),
+    "C = M' diag(rho/s) instead of diag(s/rho)": (
+        "operators.py", "mc * np.asarray(s) / np.asarray(rho)", "mc * np.asarray(rho) / np.asarray(s)",
+        "projected_system"),
+    "B takes grad phi of the wrong slice": (
+        "operators.py", "blocks[k][k] = -JtM / dt + 0.5 * Gk\n", "blocks[k][k] = -JtM / dt + 0.5 * Gk1\n",
+        "jacobian_matches"),
+    "time average in rho~ off-centre": (
+        "operators.py", "avg = 0.5 * (r[1:] + r[:-1])", "avg = 0.7 * r[1:] + 0.3 * r[:-1]", "symmetries"),
+    "B~ spatial term with the wrong sign": (
+        "operators.py", "blocks[j][j - 1] = -MJ / dt + 0.5 * S", "blocks[j][j - 1] = -MJ / dt - 0.5 * S", "btilde"),
+    "BB: y without M'^-1": (
+        "operators.py", "y = (d.A_tilde_block(rho) @ z) / np.tile(d.t.coarse.area, d.K)",
+        "y = d.A_tilde_block(rho) @ z", "exact_bb"),
+    "BB Schur approximation with the wrong sign": (
+        "operators.py", "- sp.diags(np.asarray(rho)) @ B @ Minv", "+ sp.diags(np.asarray(rho)) @ B @ Minv",
+        "exact_bb"),
+    "degenerate |w| doubled": (
+        "mesh.py", "edge_dist = np.where(degenerate, bdist, dist)", "edge_dist = np.where(degenerate, 2 * bdist, dist)",
+        "geometry"),
+    "circumcentre y with a sign error": (
+        "mesh.py", "uy = (a2 * (c[:, 0] - b[:, 0])", "uy = (a2 * (b[:, 0] - c[:, 0])", "geometry"),
+    "two children per cell given to the next parent": (
+        "mesh.py", "            parent.append(c)\n", "            parent.append(c if t[0] != ab else (c + 1) % len(tri))\n",
+        "nesting"),
+    "continuity equation with the wrong sign of the time difference": (
+        "ipm.py", "Fphi[k] = -(d.M @ (d.J @ (R[k + 1] - R[k]))) / dt", "Fphi[k] = +(d.M @ (d.J @ (R[k + 1] - R[k]))) / dt",
+        "jacobian_matches"),
+    "Hamilton-Jacobi time difference reversed": (
+        "ipm.py", "JtM @ (P[k + 1] - P[k]) / dt", "JtM @ (P[k] - P[k + 1]) / dt", "jacobian_matches"),
+    "complementarity rho s = 2 mu": (
+        "ipm.py", "Fs = R[1:-1] * S - mu", "Fs = R[1:-1] * S - 2 * mu", "uniform"),
+    "cost scaled by 1/K instead of dt": (
+        "ipm.py", "return d.dt * total", "return total / d.K", "duality_gap"),
+    "dual value with the end densities exchanged": (
+        "ipm.py", "term = float(P[-1] @ (MJ @ rho1)) - float(P[0] @ (MJ @ rho0))",
+        "term = float(P[-1] @ (MJ @ rho0)) - float(P[0] @ (MJ @ rho1))", "duality_gap"),
+    "adjoint: kinetic partial doubled": (
+        "adjoint.py", "e = [0.25 * d.dt *", "e = [0.5 * d.dt *", "adjoint_gradient_matches"),
+}
+
+
+def _copy(dst):
+    for d in ("oracle", "ot_inputs"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(dst, d),
+                        ignore=shutil.ignore_patterns("__pycache__", "*.so", "_build"))
+    os.makedirs(os.path.join(dst, "tests"))
+    for f in ("conftest.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
+
+
+def _run_pins(repo, expr):
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    env.pop("PYTHONPATH", None)
+    return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+                           "-p", "no:cacheprovider", "-k", expr], cwd=repo, env=env, capture_output=True,
+                          text=True, timeout=600)
+
+
+def test_unmutated_copy_passes_the_pins_used_below(tmp_path):
+    _copy(str(tmp_path))
+    expr = " or ".join(sorted({m[3] for m in MUTATIONS.values()}))
+    r = _run_pins(str(tmp_path), expr)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    f, old, new, expr = MUTATIONS[name]
+    _copy(str(tmp_path))
+    path = os.path.join(str(tmp_path), "oracle", f)
+    src = open(path).read()
+    assert src.count(old) == 1, "the text to mutate must occur exactly once"
+    open(path, "w").write(src.replace(old, new, 1))
+    r = _run_pins(str(tmp_path), expr)
+    assert r.returncode == 1 and " failed" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
