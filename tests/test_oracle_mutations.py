@@ -59,6 +59,16 @@ MUTATIONS = {
     "dual value with the end densities exchanged": (
         "ipm.py", "term = float(P[-1] @ (MJ @ rho1)) - float(P[0] @ (MJ @ rho0))",
         "term = float(P[-1] @ (MJ @ rho0)) - float(P[0] @ (MJ @ rho1))", "duality_gap"),
+    "Hamilton-Jacobi kinetic term doubled": (
+        "ipm.py", "+ 0.25 * (d.RT @ (g0 ** 2 + g1 ** 2))", "+ 0.5 * (d.RT @ (g0 ** 2 + g1 ** 2))",
+        "jacobian_matches"),
+    "slack enters F_rho without the coarse mass matrix": (
+        "ipm.py", "+ d.Mc @ S[k]", "+ S[k]", "jacobian_matches"),
+    "R_T weighted by |e|/|w| instead of |e||w|": (
+        "operators.py", "sp.diags(f.edge_dist * f.edge_len)", "sp.diags(f.edge_len / f.edge_dist)",
+        "symmetric_saddle"),
+    "adjoint: initial-time flux with the wrong sign": (
+        "adjoint.py", "(MJ / d.dt + flux(0))", "(MJ / d.dt - flux(0))", "adjoint_gradient_matches"),
     "adjoint: kinetic partial doubled": (
         "adjoint.py", "e = [0.25 * d.dt *", "e = [0.5 * d.dt *", "adjoint_gradient_matches"),
 }
