@@ -39,6 +39,11 @@ MUTATIONS = {
     "BB Schur approximation with the wrong sign": (
         "operators.py", "- sp.diags(np.asarray(rho)) @ B @ Minv", "+ sp.diags(np.asarray(rho)) @ B @ Minv",
         "exact_bb"),
+    "SIMPLE: Schur complement with the wrong sign of the C term": (
+        "operators.py", "S = -(P @ d.C_block(rho, s) @ P.T + Bp", "S = -(-P @ d.C_block(rho, s) @ P.T + Bp",
+        "simple_application"),
+    "SIMPLE: back substitution without A^-1": (
+        "operators.py", "return x1 - (Bp.T @ y) / Ad, y", "return x1 - Bp.T @ y, y", "simple_application"),
     "degenerate |w| doubled": (
         "mesh.py", "edge_dist = np.where(degenerate, bdist, dist)", "edge_dist = np.where(degenerate, 2 * bdist, dist)",
         "geometry"),
