@@ -73,3 +73,18 @@ def test_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower() or f == "__init__.py", f
+
+
+def test_noalloc_entry_point_checks_arguments_before_device_work(lib_path):
+    """ot_kkt_apply_noalloc rejects sizes beyond its static scratch, unsupported
+    sides and NULL arrays with OT_ERR_INVALID_ARG before it touches a device."""
+    from paper_2209_00315_gb300 import capi
+
+    lib = capi.load()
+    p = [ctypes.c_void_p(16)] * 7   # never dereferenced: every case fails its argument check first
+    assert lib.ot_kkt_apply_noalloc(8, 4097, *p, None) == 1
+    assert b"4096" in lib.ot_last_error()
+    assert lib.ot_kkt_apply_noalloc(13, 4, *p, None) == 1
+    assert lib.ot_kkt_apply_noalloc(8, 0, *p, None) == 1
+    assert lib.ot_kkt_apply_noalloc(8, 4, None, *p[1:], None) == 1
+    assert b"NULL" in lib.ot_last_error()
