@@ -256,6 +256,10 @@ ot_status ot_ipm_solve(ot_mesh* mesh, const double* rho_in, const double* rho_f,
   OT_TRY
   ot_options o = resolve(opt_in);
   require(mesh != nullptr, "mesh is NULL");
+  // checks that need no device memory come before the workspace is allocated
+  require(mu0 > 0 && tol > 0, "mu0 and tol must be positive");
+  require(rho_in && rho_f, "rho_in / rho_f is NULL");
+  require(rho && phi && s, "output arrays are NULL");
   Workspace& W = workspace(mesh, K, o);
   solve_in(W, mesh, rho_in, rho_f, mu0, tol, o, warm_start, rho, phi, s, cost, stats, cuda_stream);
   return OT_OK;

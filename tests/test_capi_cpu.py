@@ -88,3 +88,29 @@ def test_noalloc_entry_point_checks_arguments_before_device_work(lib_path):
     assert lib.ot_kkt_apply_noalloc(8, 0, *p, None) == 1
     assert lib.ot_kkt_apply_noalloc(8, 4, None, *p[1:], None) == 1
     assert b"NULL" in lib.ot_last_error()
+
+
+def test_solver_entry_points_check_arguments_before_allocating(lib_path):
+    """Bad scalars, sizes and NULL arrays are rejected before any workspace is
+    allocated, so these calls return OT_ERR_INVALID_ARG without a device."""
+    from paper_2209_00315_gb300 import capi
+
+    lib = capi.load()
+    o = capi.default_options()
+    m = capi.Mesh(4)
+    p = ctypes.c_void_p(16)   # never dereferenced
+    st = capi.ot_stats()
+    solve = lambda K, mu0, tol, r0, out: lib.ot_ipm_solve(  # noqa: E731
+        m.handle, r0, r0, K, mu0, tol, ctypes.byref(o), 0, out, out, out, None, ctypes.byref(st), None)
+    assert solve(4, 0.0, 1e-6, p, p) == 1 and b"mu0" in lib.ot_last_error()
+    assert solve(4, 1.0, -1.0, p, p) == 1
+    assert solve(0, 1.0, 1e-6, p, p) == 1 and b"K must be" in lib.ot_last_error()
+    assert solve(5000, 1.0, 1e-6, p, p) == 1
+    assert solve(4, 1.0, 1e-6, None, p) == 1 and b"NULL" in lib.ot_last_error()
+    assert solve(4, 1.0, 1e-6, p, None) == 1 and b"NULL" in lib.ot_last_error()
+    assert lib.ot_newton_solve(m.handle, 4, -1.0, p, p, p, p, p, ctypes.byref(o), p, p, p, None, None) == 1
+    assert b"mu" in lib.ot_last_error()
+    assert lib.ot_cost_grad(m.handle, 4, 1e-3, p, p, p, p, p, ctypes.byref(o), None, p, None) == 1
+    assert b"NULL" in lib.ot_last_error()
+    bad = capi.default_options(tau=1.5)
+    assert lib.ot_ipm_solve(m.handle, p, p, 4, 1.0, 1e-6, ctypes.byref(bad), 0, p, p, p, None, None, None) == 1
