@@ -180,6 +180,25 @@ ot_status ot_cost_grad(ot_mesh* mesh, int32_t K, double mu, const double* phi, c
                        const double* s, const double* rho_in, const double* rho_f, const ot_options* opt,
                        double* grad_in, double* grad_f, void* cuda_stream);
 
+/* Autotuner for the multigrid settings of the BB preconditioner (the paper
+ * fixes them once for its AGMG solves; choosing them by timed trials has no
+ * counterpart there).  For each of n_cand candidates (smooth_sweeps,
+ * coarse_sweeps, lap_cycles), given as a host array cand of 3 n_cand int32
+ * (NULL: a built-in grid of 12, n_cand ignored), one Newton direction is
+ * computed at the state (phi, rho, s) with barrier mu, as by ot_newton_solve
+ * with *opt and that candidate's settings, after one untimed solve with *opt
+ * itself.  Each trial's wall time (host clock around the solve, which returns
+ * after a stream synchronisation) goes to seconds[i] (host, nullable; the
+ * built-in grid needs 12 entries), or -1 where the solve failed.  The
+ * fastest successful candidate's three settings are written into *opt, the
+ * rest of *opt is unchanged.  The state comes in opt->memspace as in
+ * ot_newton_solve; the directions are discarded.  Choose the state from the
+ * stage whose solves dominate (late, small mu, for a full solve).  Returns the
+ * first trial's error if every candidate failed. */
+ot_status ot_tune_newton(ot_mesh* mesh, int32_t K, double mu, const double* phi, const double* rho, const double* s,
+                         const double* rho_in, const double* rho_f, ot_options* opt, int32_t n_cand,
+                         const int32_t* cand, double* seconds, void* cuda_stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* ot_last_error(void);
 

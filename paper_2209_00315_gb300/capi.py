@@ -28,7 +28,7 @@ OT_MAX_STAGES = 40
 EXPORTED = ["ot_default_options", "ot_mesh_create", "ot_mesh_destroy", "ot_mesh_info", "ot_ipm_solve",
             "ot_ipm_solve_batched", "ot_newton_solve", "ot_cost_grad", "ot_last_error", "ot_residual", "ot_kkt_apply", "ot_schur_apply",
             "ot_bb_apply", "ot_cost_dual", "ot_kernel_timing_enable", "ot_kernel_timing_count",
-            "ot_kernel_timing_read", "ot_kernel_launches", "ot_kkt_apply_noalloc"]
+            "ot_kernel_timing_read", "ot_kernel_launches", "ot_kkt_apply_noalloc", "ot_tune_newton"]
 
 
 class OTError(RuntimeError):
@@ -96,6 +96,7 @@ def load():
         "ot_newton_solve": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, C.POINTER(ot_options), _P, _P, _P,
                                  C.POINTER(ot_stats), _P]),
         "ot_cost_grad": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, C.POINTER(ot_options), _P, _P, _P]),
+        "ot_tune_newton": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, C.POINTER(ot_options), _I, _P, _P, _P]),
         "ot_last_error": (C.c_char_p, []),
         "ot_residual": (_I, [_P, _I, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_kkt_apply": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -291,6 +292,24 @@ def ot_cost_grad(mesh: Mesh, K: int, mu: float, phi, rho, s, rho_in, rho_f, opti
                                _stream(stream)))
     return gin, gf
 
+
+
+TUNE_GRID = [(sw, cs, lc) for sw in (1, 2, 3) for cs in (6, 10) for lc in (1, 2)]   # the library's built-in grid
+
+
+def ot_tune_newton(mesh: Mesh, K: int, mu: float, phi, rho, s, rho_in, rho_f, options=None, candidates=None,
+                   stream=None):
+    """Timed trials of (smooth_sweeps, coarse_sweeps, lap_cycles) on one Newton solve at the given
+    device state; returns (options with the fastest setting, seconds per candidate, -1 = failed)."""
+    o = options if options is not None else default_options()
+    o.memspace = OT_MEM_DEVICE
+    cand = list(candidates) if candidates is not None else TUNE_GRID
+    arr = (C.c_int32 * (3 * len(cand)))(*[int(v) for c in cand for v in c])
+    sec = (C.c_double * len(cand))()
+    _check(load().ot_tune_newton(mesh.handle, int(K), float(mu), _dev_ptr(phi), _dev_ptr(rho), _dev_ptr(s),
+                                 _dev_ptr(rho_in), _dev_ptr(rho_f), C.byref(o), len(cand),
+                                 C.cast(arr, C.c_void_p), C.cast(sec, C.c_void_p), _stream(stream)))
+    return o, list(sec)
 
 def ot_residual(mesh: Mesh, K: int, mu: float, phi, rho, s, rho_in, rho_f, stream=None):
     Fphi = torch.empty_like(phi)

@@ -410,6 +410,71 @@ ot_status ot_cost_grad(ot_mesh* mesh, int32_t K, double mu, const double* phi, c
   OT_CATCH
 }
 
+// ------------------------------------------------------------------ autotuner
+ot_status ot_tune_newton(ot_mesh* mesh, int32_t K, double mu, const double* phi, const double* rho, const double* s,
+                         const double* rho_in, const double* rho_f, ot_options* opt, int32_t n_cand,
+                         const int32_t* cand, double* seconds, void* cuda_stream) {
+  OT_TRY
+  require(opt != nullptr, "opt is NULL");
+  const ot_options base = resolve(opt);
+  require(mesh != nullptr, "mesh is NULL");
+  require(mu > 0, "mu must be positive");
+  require(phi && rho && s && rho_in && rho_f, "NULL argument");
+  std::vector<int32_t> grid;  // (smooth_sweeps, coarse_sweeps, lap_cycles) per candidate
+  if (cand) {
+    require(n_cand >= 1 && n_cand <= 1024, "n_cand must be in [1, 1024]");
+    grid.assign(cand, cand + 3 * (size_t)n_cand);
+  } else {
+    for (int sw = 1; sw <= 3; ++sw)
+      for (int cs : {6, 10})
+        for (int lc = 1; lc <= 2; ++lc) grid.insert(grid.end(), {sw, cs, lc});
+  }
+  const int nc = (int)(grid.size() / 3);
+  auto with = [&](int i) {
+    ot_options t = base;
+    t.smooth_sweeps = grid[3 * i];
+    t.coarse_sweeps = grid[3 * i + 1];
+    t.lap_cycles = grid[3 * i + 2];
+    return t;
+  };
+  for (int i = 0; i < nc; ++i) {  // every candidate must be a valid setting
+    const ot_options t = with(i);
+    resolve(&t);
+  }
+  ot_stats st;
+  // untimed first solve: workspace allocation and first-touch costs stay out of the trials
+  ot_status r = ot_newton_solve(mesh, K, mu, phi, rho, s, rho_in, rho_f, &base, nullptr, nullptr, nullptr, &st,
+                                cuda_stream);
+  if (r != OT_OK) return r;
+  int best = -1;
+  double tbest = 0.0;
+  ot_status err = OT_OK;
+  std::string msg;
+  for (int i = 0; i < nc; ++i) {
+    const ot_options t = with(i);
+    const double t0 = dev::now();
+    r = ot_newton_solve(mesh, K, mu, phi, rho, s, rho_in, rho_f, &t, nullptr, nullptr, nullptr, &st, cuda_stream);
+    const double el = dev::now() - t0;
+    if (r == OT_OK && st.fgmres_iters >= t.fgmres_max_iter) {  // capped: not a usable setting
+      r = OT_ERR_NOT_CONVERGED;
+      g_err = "FGMRES reached its iteration cap";
+    }
+    if (seconds) seconds[i] = r == OT_OK ? el : -1.0;
+    if (r != OT_OK) {
+      if (err == OT_OK) err = r, msg = g_err;
+      continue;
+    }
+    if (best < 0 || el < tbest) best = i, tbest = el;
+  }
+  if (best < 0) return set_err(err, "every candidate failed; first: " + msg);
+  opt->smooth_sweeps = grid[3 * best];
+  opt->coarse_sweeps = grid[3 * best + 1];
+  opt->lap_cycles = grid[3 * best + 2];
+  g_err.clear();
+  return OT_OK;
+  OT_CATCH
+}
+
 // ------------------------------------------------------------------ operator-level entry points
 // Any cached workspace of this K serves as scratch for the operator-level calls.
 static Workspace& op_workspace(ot_mesh* mesh, int K) {

@@ -114,3 +114,24 @@ def test_solver_entry_points_check_arguments_before_allocating(lib_path):
     assert b"NULL" in lib.ot_last_error()
     bad = capi.default_options(tau=1.5)
     assert lib.ot_ipm_solve(m.handle, p, p, 4, 1.0, 1e-6, ctypes.byref(bad), 0, p, p, p, None, None, None) == 1
+
+
+def test_autotuner_checks_arguments_and_candidates_before_device_work(lib_path):
+    """ot_tune_newton validates its options, state pointers and every candidate
+    setting before its first trial solve."""
+    from paper_2209_00315_gb300 import capi
+
+    lib = capi.load()
+    m = capi.Mesh(4)
+    o = capi.default_options()
+    p = ctypes.c_void_p(16)   # never dereferenced
+    cand = (ctypes.c_int32 * 6)(2, 6, 2, 2, 6, 0)   # the second candidate has lap_cycles = 0
+    tune = lambda mu, opt, n, c, phi=p: lib.ot_tune_newton(  # noqa: E731
+        m.handle, 4, mu, phi, p, p, p, p, opt, n, c, None, None)
+    assert tune(1e-3, None, 1, cand) == 1 and b"opt is NULL" in lib.ot_last_error()
+    assert tune(0.0, ctypes.byref(o), 1, cand) == 1 and b"mu" in lib.ot_last_error()
+    assert tune(1e-3, ctypes.byref(o), 1, cand, phi=None) == 1 and b"NULL" in lib.ot_last_error()
+    assert tune(1e-3, ctypes.byref(o), 0, cand) == 1 and b"n_cand" in lib.ot_last_error()
+    assert tune(1e-3, ctypes.byref(o), 2, cand) == 1 and b"cycle counts" in lib.ot_last_error()
+    assert (o.smooth_sweeps, o.coarse_sweeps, o.lap_cycles) == (2, 6, 2)   # unchanged on error
+    assert len(capi.TUNE_GRID) == 12 and (2, 6, 2) in capi.TUNE_GRID
