@@ -69,6 +69,8 @@ MUTATIONS = {
         "jacobian_matches"),
     "slack enters F_rho without the coarse mass matrix": (
         "ipm.py", "+ d.Mc @ S[k]", "+ S[k]", "jacobian_matches"),
+    "slack weighted by 1/N' instead of the cell areas (equal on the uniform grid)": (
+        "ipm.py", "+ d.Mc @ S[k]", "+ S[k] / d.Nc", "exact_solution_on_a_graded_mesh"),
     "R_T weighted by |e|/|w| instead of |e||w|": (
         "operators.py", "sp.diags(f.edge_dist * f.edge_len)", "sp.diags(f.edge_len / f.edge_dist)",
         "symmetric_saddle"),

@@ -111,18 +111,24 @@ def test_operator_identities():
     assert np.allclose(d.RE @ np.ones(d.Nc), 1.0)
 
 
+def _graded_discretisation(n, K):
+    """The n x n diagonal grid of the unit square with x moved to x + 0.15 x (1 - x):
+    the domain and its area stay the same, the coarse cells' areas differ."""
+    xy, tri = mesh.square_grid(n)
+    xy = xy.copy()
+    xy[:, 0] += 0.15 * xy[:, 0] * (1.0 - xy[:, 0])
+    fxy, ftri, parent = mesh.refine4(xy, tri)
+    t = mesh.TwoLevelMesh(mesh.build_mesh(xy, tri), mesh.build_mesh(fxy, ftri), parent, n)
+    return ops.Discretisation(t, K)
+
+
 def test_operator_identities_on_a_graded_mesh():
     """The same identities where the coarse cells differ in area (the grid stretched
     along x), which tells P = I - M' E'^T E'/|Omega| from its transpose: P kills
     the per-slice mass vectors M'E'^T, P^T y has zero mass in every slice, P^2 = P,
     and J^T M J = M' for any midpoint 4-split."""
-    xy, tri = mesh.square_grid(3)
-    xy = xy.copy()
-    xy[:, 0] += 0.15 * xy[:, 0] * (1.0 - xy[:, 0])
-    fxy, ftri, parent = mesh.refine4(xy, tri)
-    t = mesh.TwoLevelMesh(mesh.build_mesh(xy, tri), mesh.build_mesh(fxy, ftri), parent, 3)
-    d = ops.Discretisation(t, 2)
-    area = t.coarse.area
+    d = _graded_discretisation(3, 2)
+    area = d.t.coarse.area
     assert area.max() - area.min() > 0.01
     P = d.P_block().toarray()
     mcE = np.kron(np.eye(d.K), area[:, None])
@@ -472,6 +478,28 @@ def test_uniform_densities_exact_solution():
     assert np.allclose(res.phi, expect, atol=1e-14)
     assert abs(res.cost) < 1e-25
     assert np.isclose(res.cost - res.dual, mu * K / (K + 1), rtol=1e-12)
+
+
+def test_uniform_densities_exact_solution_on_a_graded_mesh():
+    """The same closed form where the coarse cells differ in area.  With phi constant
+    in space, J^T M 1 = |c'| and the slack enters F_rho as M' s, so every term of
+    F_rho is a multiple of the area vector and rho^k = c, s = mu/c still solve the
+    system.  A slack weighted by anything other than the cell areas (1/N', say, which
+    equals M' on the uniform grid) leaves a spatially varying F_rho and moves rho."""
+    n, K, c = 3, 3, 1.0
+    d = _graded_discretisation(n, K)
+    assert np.ptp(d.t.coarse.area) > 0.01 and abs(d.area_total - 1.0) < 1e-14
+    r0 = np.full(d.Nc, c)
+    res = ipm.ipm_solve(d, r0, r0.copy(), ipm.IPMOptions(final_newton_tol=1e-12))
+    mu = res.mu
+    assert all(steps == 1 for _, steps, _ in res.stages)
+    assert np.allclose(res.rho, c, rtol=0, atol=1e-13)
+    assert np.allclose(res.s, mu / c, rtol=1e-12)
+    k = np.arange(K + 1)
+    expect = ipm.phi_gauge(d, np.repeat(-k * d.dt * mu / c, d.N))
+    assert np.allclose(res.phi, expect, atol=1e-14)
+    assert abs(res.cost) < 1e-25
+    assert np.isclose(res.cost - res.dual, mu * d.area_total * K / (K + 1), rtol=1e-12)
 
 
 def test_mu_schedule_matches_table3():
