@@ -44,10 +44,11 @@ def workload_config(args, world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "precision": args.precision, "n": n, "K": K,
             "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
             "unknowns": (K + 1) * 8 * n * n + K * 2 * n * n}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in profiles/ (None if the
-# kernel changed since it was taken): schur_line_smooth = mean over 48 consecutive launches of
-# k_line_pcr_tile_kernel (all three levels and sweep modes), profiles/k_line_pcr_tile_mix64.md
-NCU_TRAFFIC = {"schur_line_smooth": 1372256.0}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, by kernel group, from an ncu capture of the
+# kernel as it is built now; a group without an entry reports traffic None.  schur_line_smooth has none:
+# its capture (profiles/k_line_pcr_tile_mix64.md, 1.372 MB per launch) predates the move of
+# k_line_pcr_tile_kernel's body into inlined stage functions.
+NCU_TRAFFIC: dict = {}
 
 
 def parse_args():
