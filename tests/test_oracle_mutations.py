@@ -16,7 +16,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# (file under oracle/, text, replacement, pins (-k expression) that must catch it)
+# (file under oracle/, text, replacement, pins (-k expression) that must catch it); a mistake that
+# has to be made in several places at once to stay self-consistent lists its edits in EDITS instead.
 MUTATIONS = {
     "gradient divides by |e| instead of |w|": (
         "operators.py", "sp.diags(1.0 / m.edge_dist) @ incidence(m).T", "sp.diags(1.0 / m.edge_len) @ incidence(m).T",
@@ -80,6 +81,22 @@ MUTATIONS = {
         "adjoint.py", "e = [0.25 * d.dt *", "e = [0.5 * d.dt *", "adjoint_gradient_matches"),
 }
 
+# ([(file, text, replacement), ...], pins): the same mistake made consistently in the residual and in
+# the Jacobian, so that the Jacobian-versus-differences pin cannot see it
+EDITS = {
+    "time term of F_rho as M'J^T (the printed order) in F_rho and in B": (
+        [("ipm.py", "JtM = d.J.T @ d.M", "JtM = d.Mc @ d.J.T"),
+         ("operators.py", "JtM = (self.J.T @ self.M).tocsr()", "JtM = (self.Mc @ self.J.T).tocsr()")],
+        "symmetric_saddle"),
+    "slack weighted by 1/N' in F_rho, in the Jacobian and in C": (
+        [("ipm.py", "+ d.Mc @ S[k]", "+ S[k] / d.Nc"),
+         ("operators.py", "return sp.diags(np.tile(self.t.coarse.area, self.K))",
+          "return sp.diags(np.full(self.K * self.Nc, 1.0 / self.Nc))"),
+         ("operators.py", "mc = np.tile(self.t.coarse.area, self.K)\n        return sp.diags(mc * np.asarray(s)",
+          "mc = np.full(self.K * self.Nc, 1.0 / self.Nc)\n        return sp.diags(mc * np.asarray(s)")],
+        "exact_solution_on_a_graded_mesh"),
+}
+
 
 def _copy(dst):
     for d in ("oracle", "ot_inputs"):
@@ -101,18 +118,27 @@ def _run_pins(repo, expr):
 
 def test_unmutated_copy_passes_the_pins_used_below(tmp_path):
     _copy(str(tmp_path))
-    expr = " or ".join(sorted({m[3] for m in MUTATIONS.values()}))
+    expr = " or ".join(sorted({m[3] for m in MUTATIONS.values()} | {m[1] for m in EDITS.values()}))
     r = _run_pins(str(tmp_path), expr)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
 
 
-@pytest.mark.parametrize("name", list(MUTATIONS))
+def _plant(repo, edits):
+    for f, old, new in edits:
+        path = os.path.join(repo, "oracle", f)
+        src = open(path).read()
+        assert src.count(old) == 1, "the text to mutate must occur exactly once"
+        open(path, "w").write(src.replace(old, new, 1))
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS) + list(EDITS))
 def test_planted_mistake_fails_a_pin(tmp_path, name):
-    f, old, new, expr = MUTATIONS[name]
+    if name in MUTATIONS:
+        f, old, new, expr = MUTATIONS[name]
+        edits = [(f, old, new)]
+    else:
+        edits, expr = EDITS[name]
     _copy(str(tmp_path))
-    path = os.path.join(str(tmp_path), "oracle", f)
-    src = open(path).read()
-    assert src.count(old) == 1, "the text to mutate must occur exactly once"
-    open(path, "w").write(src.replace(old, new, 1))
+    _plant(str(tmp_path), edits)
     r = _run_pins(str(tmp_path), expr)
     assert r.returncode == 1 and " failed" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
