@@ -32,6 +32,11 @@ MUTATIONS = {
         "jacobian_matches"),
     "time average in rho~ off-centre": (
         "operators.py", "avg = 0.5 * (r[1:] + r[:-1])", "avg = 0.7 * r[1:] + 0.3 * r[:-1]", "symmetries"),
+    "end densities exchanged in the space-time density array": (
+        "operators.py", "return np.vstack([rho0[None, :], self.rho_slices(rho), rho1[None, :]])",
+        "return np.vstack([rho1[None, :], self.rho_slices(rho), rho0[None, :]])", "duality_gap"),
+    "rho~ from the later slice alone instead of the time average": (
+        "operators.py", "avg = 0.5 * (r[1:] + r[:-1])", "avg = r[1:]", "jacobian_matches"),
     "B~ spatial term with the wrong sign": (
         "operators.py", "blocks[j][j - 1] = -MJ / dt + 0.5 * S", "blocks[j][j - 1] = -MJ / dt - 0.5 * S", "btilde"),
     "BB: y without M'^-1": (
