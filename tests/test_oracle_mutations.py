@@ -65,6 +65,9 @@ MUTATIONS = {
         "ipm.py", "JtM @ (P[k + 1] - P[k]) / dt", "JtM @ (P[k] - P[k + 1]) / dt", "jacobian_matches"),
     "complementarity rho s = 2 mu": (
         "ipm.py", "Fs = R[1:-1] * S - mu", "Fs = R[1:-1] * S - 2 * mu", "uniform"),
+    "stopping rule compares mu with the tolerance, without the gap's factor |Omega| K/(K+1)": (
+        "ipm.py", "while mu * area_total * K / (K + 1) > opt.gap_tol", "while mu * area_total > opt.gap_tol",
+        "stops_at_the_first_stage"),
     "cost scaled by 1/K instead of dt": (
         "ipm.py", "return d.dt * total", "return total / d.K", "duality_gap"),
     "dual value with the end densities exchanged": (

@@ -512,6 +512,24 @@ def test_mu_schedule_matches_table3():
         assert float(f"{mu:.0e}") == lab
 
 
+def test_ipm_stops_at_the_first_stage_whose_duality_gap_meets_the_tolerance():
+    """The solve stops at the first mu whose barrier solution has C - D <= tol, with
+    C and D computed from that solution.  With K = 1 the gap is mu/2, so a rule that
+    compares mu itself with tol would run one stage further (tol = 1e-3: 3.2e-4 in
+    place of 1.6e-3).  The previous stage's gap comes from its own barrier solution,
+    solved alone from the initial point."""
+    n, K, tol = 2, 1, 1e-3
+    d = ipm.discretise(n, K)
+    r0 = make_density(n, [(0.3, 0.3)], [0.15], [1.0], 1e-3)
+    r1 = make_density(n, [(0.7, 0.6)], [0.15], [1.0], 1e-3)
+    res = ipm.ipm_solve(d, r0, r1, ipm.IPMOptions(gap_tol=tol, final_newton_tol=1e-12))
+    mus = [m for m, _, _ in res.stages]
+    assert len(mus) >= 2 and res.cost - res.dual <= tol
+    prev = ipm.ipm_solve(d, r0, r1, ipm.IPMOptions(mu0=mus[-2], gap_tol=1e9, final_newton_tol=1e-12))
+    assert len(prev.stages) == 1 and prev.mu == mus[-2]
+    assert prev.cost - prev.dual > tol
+
+
 @pytest.fixture(scope="module")
 def converged_small():
     n, K = 4, 4
