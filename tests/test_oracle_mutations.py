@@ -68,6 +68,9 @@ MUTATIONS = {
     "stopping rule compares mu with the tolerance, without the gap's factor |Omega| K/(K+1)": (
         "ipm.py", "while mu * area_total * K / (K + 1) > opt.gap_tol", "while mu * area_total > opt.gap_tol",
         "stops_at_the_first_stage"),
+    "fraction to the boundary over rho alone, not over s": (
+        "ipm.py", "alpha = min(step_length(rho, drho, opt.tau), step_length(s, ds, opt.tau))",
+        "alpha = step_length(rho, drho, opt.tau)", "barycentre"),
     "cost scaled by 1/K instead of dt": (
         "ipm.py", "return d.dt * total", "return total / d.K", "duality_gap"),
     "dual value with the end densities exchanged": (
