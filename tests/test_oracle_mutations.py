@@ -53,6 +53,9 @@ MUTATIONS = {
     "degenerate |w| doubled": (
         "mesh.py", "edge_dist = np.where(degenerate, bdist, dist)", "edge_dist = np.where(degenerate, 2 * bdist, dist)",
         "geometry"),
+    "edge weight lambda measured from the right cell's point (1/2 on the right-triangle grid)": (
+        "mesh.py", "d_left = _point_line_distance(centre[left], va, vb)",
+        "d_left = _point_line_distance(centre[right], va, vb)", "circumcentric"),
     "circumcentre y with a sign error": (
         "mesh.py", "uy = (a2 * (c[:, 0] - b[:, 0])", "uy = (a2 * (b[:, 0] - c[:, 0])", "geometry"),
     "two children per cell given to the next parent": (

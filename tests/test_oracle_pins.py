@@ -59,6 +59,47 @@ def test_geometry_closed_form(n):
         assert np.allclose(tm.edge_lambda, 0.5)
 
 
+def test_edge_weights_satisfy_the_circumcentric_identity_on_an_acute_mesh():
+    """Reading R2 on a generic mesh.  For a triangle K with its circumcentre, the
+    distances d_{K,e} to its three edges satisfy sum_e |e| d_{K,e} n_e n_e^T = |K| I
+    (the circumcentric form of the divergence theorem).  With lambda_e = d_{K,e}/|w_e|
+    on the left cell and 1 - lambda_e on the right, every acute triangle whose three
+    edges are interior must reproduce |K| I.  On the right-triangle grid lambda is
+    1/2 everywhere, so only an irregular mesh can tell the two cells apart: a
+    jittered triangular lattice, Delaunay-triangulated."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(3)
+    h = 0.125
+    lattice = np.array([((i + 0.5 * (j % 2)) * h, j * h * np.sqrt(3) / 2) for j in range(10) for i in range(10)])
+    xy = lattice + rng.uniform(-0.12, 0.12, lattice.shape) * h
+    tri = Delaunay(xy).simplices.copy()
+    p = xy[tri]
+    e1, e2 = p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]
+    cw = e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0] < 0
+    tri[cw] = tri[cw][:, [0, 2, 1]]
+    p = xy[tri]
+    # acute: at every vertex the two edges leaving it have a positive dot product
+    acute = np.min([np.einsum("ij,ij->i", p[:, (k + 1) % 3] - p[:, k], p[:, (k + 2) % 3] - p[:, k])
+                    for k in range(3)], 0) > 1e-3 * h * h
+    m = mesh.build_mesh(xy, tri)
+    assert not m.degenerate.any()
+    T = np.zeros((m.ncell, 2, 2))
+    count = np.zeros(m.ncell, dtype=int)
+    for e, (L, R) in enumerate(m.edge_cells):
+        w = m.centre[R] - m.centre[L]
+        nn = np.outer(w, w) / float(w @ w)
+        T[L] += m.edge_len[e] * m.edge_lambda[e] * m.edge_dist[e] * nn
+        T[R] += m.edge_len[e] * (1.0 - m.edge_lambda[e]) * m.edge_dist[e] * nn
+        count[L] += 1
+        count[R] += 1
+    sel = (count == 3) & acute
+    assert sel.sum() > 100
+    assert np.abs(T[sel] - m.area[sel, None, None] * np.eye(2)).max() < 1e-12 * m.area[sel].max()
+    # the weights are not all 1/2 here, so the test can see which cell is which
+    assert np.ptp(m.edge_lambda[sel[m.edge_cells[:, 0]] & sel[m.edge_cells[:, 1]]]) > 0.1
+
+
 def test_effective_conductivity_closed_form():
     """Homogenised x-conductivity of the unit-coefficient TPFA Laplacian on this mesh.
 
