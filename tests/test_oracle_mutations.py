@@ -39,6 +39,12 @@ MUTATIONS = {
         "operators.py", "avg = 0.5 * (r[1:] + r[:-1])", "avg = r[1:]", "jacobian_matches"),
     "B~ spatial term with the wrong sign": (
         "operators.py", "blocks[j][j - 1] = -MJ / dt + 0.5 * S", "blocks[j][j - 1] = -MJ / dt - 0.5 * S", "btilde"),
+    "B~ time term with the wrong sign on the current slice": (
+        "operators.py", "blocks[j][j] = MJ / dt + 0.5 * S", "blocks[j][j] = -MJ / dt + 0.5 * S", "btilde"),
+    "A~^k from the time average of rho^k and rho^(k+1) instead of rho^k": (
+        "operators.py", "return sp.block_diag([weighted_laplacian(c, Rc @ R[k]) for k in range(self.K)]).tocsr()",
+        "return sp.block_diag([weighted_laplacian(c, Rc @ (0.5 * (R[k] + R[min(k + 1, self.K - 1)])))"
+        " for k in range(self.K)]).tocsr()", "depends_on_rho_k"),
     "BB: y without M'^-1": (
         "operators.py", "y = (d.A_tilde_block(rho) @ z) / np.tile(d.t.coarse.area, d.K)",
         "y = d.A_tilde_block(rho) @ z", "exact_bb"),

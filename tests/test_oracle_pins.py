@@ -298,6 +298,30 @@ def test_atilde_is_half_the_galerkin_product_of_A(n, K):
         assert np.abs(0.5 * G[blk, blk] - At[blk, blk]).max() < 1e-13 * np.abs(At).max()
 
 
+@pytest.mark.parametrize("n,K", [(2, 3), (3, 3)])
+def test_atilde_slice_k_depends_on_rho_k_alone(n, K):
+    """Sec. 4.3.3 builds A~^k from rho^k only.  With rho varying in time, the k-th
+    block of A~ must equal half the Galerkin product J^T A J of a fine Laplacian
+    whose edge densities come from rho^k alone (the constant-in-time identity above
+    applied to each slice on its own), and no other slice of rho may move it."""
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(20 * n + K)
+    rho = rng.uniform(0.5, 2, K * d.Nc)
+    R = rho.reshape(K, d.Nc)
+    At = d.A_tilde_block(rho).toarray()
+    J1 = d.J_block(1)
+    Nc = d.Nc
+    for k in range(K):
+        Ak = d.A_block(np.tile(R[k], K), R[k], R[k]).tocsr()[: d.N, : d.N]  # slice 1, built from rho^k alone
+        G = (J1.T @ Ak @ J1).toarray()
+        blk = slice(k * Nc, (k + 1) * Nc)
+        assert np.abs(0.5 * G - At[blk, blk]).max() < 1e-13 * np.abs(At).max(), k
+        other = rho.copy().reshape(K, Nc)
+        other[np.arange(K) != k] *= rng.uniform(0.5, 2, (K - 1, Nc))
+        At2 = d.A_tilde_block(other.ravel()).toarray()
+        assert np.abs(At2[blk, blk] - At[blk, blk]).max() == 0.0, k
+
+
 @pytest.mark.parametrize("n,K", [(2, 2), (3, 3)])
 def test_btilde_is_the_block_transpose_of_B_on_coarse_functions(n, K):
     """Reading R5 with R_T = R_E^T diag(|w||e|) and lambda = 1/2 gives
