@@ -45,6 +45,9 @@ MUTATIONS = {
         "operators.py", "return sp.block_diag([weighted_laplacian(c, Rc @ R[k]) for k in range(self.K)]).tocsr()",
         "return sp.block_diag([weighted_laplacian(c, Rc @ (0.5 * (R[k] + R[min(k + 1, self.K - 1)])))"
         " for k in range(self.K)]).tocsr()", "depends_on_rho_k"),
+    "B~ spatial term with grad phi of the previous slice": (
+        "operators.py", "S = (Rf.T @ sp.diags(self.W * (self.grad @ P[j])) @ self.grad @ self.J).tocsr()",
+        "S = (Rf.T @ sp.diags(self.W * (self.grad @ P[max(j - 1, 0)])) @ self.grad @ self.J).tocsr()", "btilde"),
     "BB: y without M'^-1": (
         "operators.py", "y = (d.A_tilde_block(rho) @ z) / np.tile(d.t.coarse.area, d.K)",
         "y = d.A_tilde_block(rho) @ z", "exact_bb"),
@@ -97,6 +100,8 @@ MUTATIONS = {
         "symmetric_saddle"),
     "adjoint: initial-time flux with the wrong sign": (
         "adjoint.py", "(MJ / d.dt + flux(0))", "(MJ / d.dt - flux(0))", "adjoint_gradient_matches"),
+    "adjoint: final-time flux with the wrong sign": (
+        "adjoint.py", "(-MJ / d.dt + flux(d.K))", "(-MJ / d.dt - flux(d.K))", "adjoint_gradient_matches"),
     "adjoint: kinetic partial doubled": (
         "adjoint.py", "e = [0.25 * d.dt *", "e = [0.5 * d.dt *", "adjoint_gradient_matches"),
 }
