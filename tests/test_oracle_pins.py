@@ -87,8 +87,9 @@ def test_edge_weights_satisfy_the_circumcentric_identity_on_an_acute_mesh():
     T = np.zeros((m.ncell, 2, 2))
     count = np.zeros(m.ncell, dtype=int)
     for e, (L, R) in enumerate(m.edge_cells):
-        w = m.centre[R] - m.centre[L]
-        nn = np.outer(w, w) / float(w @ w)
+        a, b = sorted(set(tri[L].tolist()) & set(tri[R].tolist()))  # the edge's two vertices
+        t = xy[b] - xy[a]
+        nn = np.outer([t[1], -t[0]], [t[1], -t[0]]) / float(t @ t)  # unit normal from the vertices
         T[L] += m.edge_len[e] * m.edge_lambda[e] * m.edge_dist[e] * nn
         T[R] += m.edge_len[e] * (1.0 - m.edge_lambda[e]) * m.edge_dist[e] * nn
         count[L] += 1
