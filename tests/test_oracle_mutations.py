@@ -75,6 +75,9 @@ MUTATIONS = {
         "jacobian_matches"),
     "Hamilton-Jacobi time difference reversed": (
         "ipm.py", "JtM @ (P[k + 1] - P[k]) / dt", "JtM @ (P[k] - P[k + 1]) / dt", "jacobian_matches"),
+    "complementarity row of the Jacobian with diag(s) and diag(rho) exchanged": (
+        "ipm.py", "[Z(Nr, Np), sp.diags(np.asarray(s)), sp.diags(np.asarray(rho))],",
+        "[Z(Nr, Np), sp.diags(np.asarray(rho)), sp.diags(np.asarray(s))],", "jacobian_matches"),
     "complementarity rho s = 2 mu": (
         "ipm.py", "Fs = R[1:-1] * S - mu", "Fs = R[1:-1] * S - 2 * mu", "uniform"),
     "stopping rule compares mu with the tolerance, without the gap's factor |Omega| K/(K+1)": (
