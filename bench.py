@@ -230,10 +230,12 @@ def run_ours(args, world, rank, local):
             capi.ot_kernel_timing_enable(False)
         return ms, res, launches, timing
 
-    # 1. which kernel group dominates (one untimed profiled solve, all groups on)
-    capi.ot_ipm_solve(mesh, r0d, r1d, K, options=capi.default_options(precision=args.precision))
+    # 1. which kernel group dominates (one untimed profiled solve, all groups on; per-launch
+    #    events need the launches issued one by one, so this solve runs without graphs)
+    eager = capi.default_options(precision=args.precision, graphs=0)
+    capi.ot_ipm_solve(mesh, r0d, r1d, K, options=eager)
     capi.ot_kernel_timing_enable(True)
-    capi.ot_ipm_solve(mesh, r0d, r1d, K, options=capi.default_options(precision=args.precision))
+    capi.ot_ipm_solve(mesh, r0d, r1d, K, options=eager)
     torch.cuda.synchronize()
     prof_all = capi.ot_kernel_timing_read()
     capi.ot_kernel_timing_enable(False)

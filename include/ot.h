@@ -71,9 +71,9 @@ typedef enum { OT_PREC_FP64 = 0, OT_PREC_MIXED = 1 } ot_precision;
 /* Solver options; ot_default_options() fills the values used by the paper. */
 typedef struct {
   int32_t memspace;         /* OT_MEM_DEVICE or OT_MEM_HOST */
-  int32_t precision;        /* OT_PREC_FP64: FP64 arithmetic, except that the outer FGMRES takes its
-                               Gram-Schmidt coefficients from an FP32 copy of the basis (applied in
-                               FP64); OT_PREC_MIXED: also the BB preconditioner in FP32 */
+  int32_t precision;        /* OT_PREC_FP64: FP64 arithmetic throughout (with gs_shadow = 1 the outer
+                               FGMRES takes its Gram-Schmidt coefficients from an FP32 copy of the basis
+                               and applies them in FP64); OT_PREC_MIXED: the BB preconditioner in FP32 */
   double mu_factor;         /* mu_{l+1} = mu_factor mu_l (0.2) */
   double tau;               /* fraction to the boundary (0.99) */
   double newton_tol;        /* Newton stop: ||F|| <= newton_tol max(1, ||F_stage_start||) (1e-6) */
@@ -91,6 +91,14 @@ typedef struct {
   int32_t coarse_sweeps;    /* smoothing sweeps on the coarsest grid */
   int32_t max_newton;       /* Newton steps per mu stage */
   int32_t verbose;          /* 0: silent; 1: one line per stage on stderr; 2: per Newton step */
+  int32_t gs_shadow;        /* 1 (default): the outer Gram-Schmidt dot products read an FP32 copy of the
+                               FGMRES basis (coefficients applied to the FP64 basis, so the Arnoldi
+                               relation stays FP64); 0: every Gram-Schmidt pass in FP64 */
+  int32_t graphs;           /* 1 (default): each FGMRES cycle, with the inner Schur solves of its
+                               preconditioner applications, runs as one CUDA graph whose loops are
+                               conditional (WHILE) nodes driven by device-side convergence tests;
+                               0: the same kernels launched one by one, the host reading the
+                               convergence state after every Krylov step */
 } ot_options;
 
 #define OT_MAX_STAGES 40

@@ -10,7 +10,7 @@ and each Newton step solves the Jacobian system (Eq. newton-linsys) exactly by
 sparse LU, with the potential's free constant (Remark kernel) fixed by
 sum(M dphi) = 0 after grounding one potential unknown.
 
-Readings (listed in the design notes):
+Readings taken where the paper is silent, ambiguous or inconsistent:
   R4  the barrier weighs cell i of the density mesh by |c'_i|.
   R6  Newton stops at ||(F_phi; F_rho; F_s - mu)||_2 <= tol * max(1, ||F at stage start||).
   R7  mu_{l+1} = mu_l / 5 from mu_0; stop after the first stage whose gap

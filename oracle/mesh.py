@@ -8,7 +8,7 @@ without using the structure of the square grid.  The only structured step is
 the canonical renumbering of the refined mesh, which locates each fine
 triangle by its centroid.
 
-Readings of the paper (listed in the design notes):
+Readings taken where the paper is silent, ambiguous or inconsistent:
   R1  cell points are circumcentres (Sec. 2.1).  On right triangles two cells
       that share a hypotenuse have the same circumcentre; for such an edge
       (|w| < 1e-12 |e|) the distance |w| is replaced by the distance between

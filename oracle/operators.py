@@ -9,7 +9,7 @@ matrix built entry by entry from the definitions; vectors are slice-major:
 phi = (phi^1; ...; phi^{K+1}) with N entries per slice, rho and s = (.^1; ...;
 .^K) with N' entries per slice.
 
-Readings (listed in the design notes):
+Readings taken where the paper is silent, ambiguous or inconsistent:
   R3  the time term of F_rho is J^T M (phi^{k+1}-phi^k)/dt, the form that makes
       the Jacobian the symmetric block  [A B^T; B 0]  of Sec. 3.
   R5  G^k maps fine edges to coarse cells; the matrix B~ of Sec. 4.3.2 is read as

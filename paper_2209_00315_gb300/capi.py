@@ -47,7 +47,8 @@ class ot_options(C.Structure):
                 ("eps_out", C.c_double), ("final_eps_out", C.c_double), ("eps_schur", C.c_double),
                 ("fgmres_restart", C.c_int32), ("fgmres_max_iter", C.c_int32), ("schur_max_iter", C.c_int32),
                 ("lap_cycles", C.c_int32), ("smooth_sweeps", C.c_int32), ("coarse_sweeps", C.c_int32),
-                ("max_newton", C.c_int32), ("verbose", C.c_int32)]
+                ("max_newton", C.c_int32), ("verbose", C.c_int32), ("gs_shadow", C.c_int32),
+                ("graphs", C.c_int32)]
 
 
 class ot_stats(C.Structure):

@@ -73,6 +73,8 @@ void ot_default_options(ot_options* o) {
   o->coarse_sweeps = 6;
   o->max_newton = 50;
   o->verbose = 0;
+  o->gs_shadow = 1;
+  o->graphs = 1;
 }
 
 const char* ot_last_error(void) { return g_err.c_str(); }
@@ -102,6 +104,8 @@ static ot_options resolve(const ot_options* o) {
   require(r.schur_max_iter >= 1 && r.schur_max_iter <= 480, "options.schur_max_iter must be in [1, 480]");
   require(r.lap_cycles >= 1 && r.smooth_sweeps >= 0 && r.coarse_sweeps >= 1, "multigrid cycle counts");
   require(r.max_newton >= 1, "options.max_newton");
+  require(r.gs_shadow == 0 || r.gs_shadow == 1, "options.gs_shadow must be 0 or 1");
+  require(r.graphs == 0 || r.graphs == 1, "options.graphs must be 0 or 1");
   return r;
 }
 
@@ -392,15 +396,10 @@ ot_status ot_cost_grad(ot_mesh* mesh, int32_t K, double mu, const double* phi, c
   // J^T lambda = dC/du reduces (eliminating lambda_s) to the symmetric saddle system (Sec. 3.1)
   ot::k_adjoint_rhs(W.d, W.phi, W.rho, W.r0, W.r1, W.rhs, W.gsum, st);
   ot::refresh_coefficients(W, st);
-  double nb = 0.0;
-  {
-    ot::k_dot(W.rhs, W.rhs, W.ntot, W.scal + 40, W.partial, st);
-    dev::copy_d2h(W.host, W.scal + 40, sizeof(double), st);
-    dev::sync(st);
-    nb = sqrt(W.host[0]);
-  }
+  // tolerance relative to |rhs| (squared norm left in device memory for the solver)
+  ot::k_dot(W.rhs, W.rhs, W.ntot, W.scal + 40, W.partial, st);
   double eps = o.final_eps_out > 0 ? o.final_eps_out : o.eps_out;
-  ot::fgmres(W, o, W.rhs, W.sol, eps * nb, st);
+  ot::fgmres(W, o, W.rhs, W.sol, eps, W.scal + 40, 1, st);
   ot::recover_direction(W, st);
   ot::k_adjoint_grad(W.d, W.phi, W.sol, W.u, W.u + W.d.Nc, st);
   copy_out(grad_in, W.u, W.d.Nc, o, st);

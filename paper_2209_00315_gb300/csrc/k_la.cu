@@ -29,6 +29,8 @@ bool enabled = false;
 unsigned mask = 0;
 std::atomic<long long> n_launch{0};
 thread_local bool suspended = false;
+thread_local bool capturing = false;
+thread_local long long t_captured = 0;
 int stride = 1;
 namespace {
 unsigned long long seen[COUNT] = {0};
@@ -58,14 +60,14 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 void begin(int id, Stream s) {
-  if (!enabled || suspended || !((mask >> id) & 1u)) return;
+  if (!enabled || suspended || capturing || !((mask >> id) & 1u)) return;
   if (++seen[id] % (unsigned long long)stride != 0) return;
   cudaEvent_t e = get_event();
   cudaEventRecord(e, cs(s));
   open[id] = e;
 }
 void end(int id, Stream s, double bytes) {
-  if (!enabled || suspended || !open[id]) return;
+  if (!enabled || suspended || capturing || !open[id]) return;
   cudaEvent_t e = get_event();
   cudaEventRecord(e, cs(s));
   pending.push_back({id, open[id], e, bytes});

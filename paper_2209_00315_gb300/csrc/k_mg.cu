@@ -956,6 +956,23 @@ size_t k_mg_fused_smem(int S, const LevelView<T>* levels, int nlev) {
 }
 
 template <typename T>
+void k_mg_prepare_lower_cycle(int S, const LevelView<T>* levels, int nlev) {
+  const size_t bytes = k_mg_fused_smem(S, levels, nlev);
+  if (bytes > kFusedSmemLimit) throw Error(1, "fused multigrid levels exceed shared memory");
+  if (!levels[0].tau) {
+    set_smem(k_lap_lower_kernel<T>, bytes);
+    return;
+  }
+  const int kpl = pcr_kpl(S);
+  if (kpl == 1)
+    set_smem(k_sch_lower_kernel<T, 1>, bytes);
+  else if (kpl == 2)
+    set_smem(k_sch_lower_kernel<T, 2>, bytes);
+  else if (kpl == 4)
+    set_smem(k_sch_lower_kernel<T, 4>, bytes);
+}
+
+template <typename T>
 void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int nuc, T* line_c, T* line_r, T* agg,
                       Stream st) {
   (void)line_c, (void)line_r, (void)agg;
@@ -1027,6 +1044,7 @@ void k_mg_store(const T* x, double* dst, i64 n, Stream st) {
   template void k_mg_prolong<T>(int, const LevelView<T>&, const LevelView<T>&, Stream);                        \
   template void k_mg_coarse_solve<T>(int, const LevelView<T>&, int, T*, T*, T*, Stream);                       \
   template void k_mg_lower_cycle<T>(int, const LevelView<T>*, int, int, int, T*, T*, T*, Stream);              \
+  template void k_mg_prepare_lower_cycle<T>(int, const LevelView<T>*, int);                                    \
   template size_t k_mg_fused_smem<T>(int, const LevelView<T>*, int);                                           \
   template void k_mg_load<T>(const double*, double, T*, T*, i64, Stream);                                      \
   template void k_mg_store<T>(const T*, double*, i64, Stream);

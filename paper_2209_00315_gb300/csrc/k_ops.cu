@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "launch.cuh"
 #include "ot_internal.h"
 
@@ -159,19 +161,24 @@ void k_kkt_apply(const Dims& d, const double* kc, const double* x, double* y, do
 // The slice means of x_rho live in this array instead of caller- or
 // library-allocated memory; every GPU that loads the library holds it.
 static __device__ __align__(256) double g_kkt_scratch[kStaticKktMaxK];
-static double* g_kkt_scratch_addr[kStaticKktMaxDevices];  // device address per device, set up once
+// Device address of the array per device, looked up once per device with that
+// device current.  The lookup runs under a per-device once-flag, so two host
+// threads making their first call on one device at the same time do not race.
+static double* g_kkt_scratch_addr[kStaticKktMaxDevices];
+static std::once_flag g_kkt_scratch_once[kStaticKktMaxDevices];
 
 double* kkt_static_scratch() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) throw Error(7, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kStaticKktMaxDevices) throw Error(1, "device index beyond the static scratch table");
-  if (!g_kkt_scratch_addr[dev]) {
+  // a failed lookup throws out of call_once, which leaves the flag unset: the next call retries
+  std::call_once(g_kkt_scratch_once[dev], [dev]() {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_kkt_scratch);
-    if (e != cudaSuccess) throw Error(7, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    const cudaError_t r = cudaGetSymbolAddress(&p, g_kkt_scratch);
+    if (r != cudaSuccess) throw Error(7, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(r));
     g_kkt_scratch_addr[dev] = static_cast<double*>(p);
-  }
+  });
   return g_kkt_scratch_addr[dev];
 }
 

@@ -1,5 +1,6 @@
 // launch.cuh -- every kernel launch of the library goes through launch(), which
-// counts it (prof::n_launch) before the <<<>>> launch on the given stream.
+// counts it (prof::n_launch; into a graph: prof::t_captured) before the <<<>>>
+// launch on the given stream.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -45,7 +46,10 @@ __device__ __forceinline__ double strided_sum(const T* xs, long long n) {
 
 template <typename... KArgs, typename... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
-  ++prof::n_launch;
+  if (prof::capturing)
+    ++prof::t_captured;  // counted when the graph runs
+  else
+    ++prof::n_launch;
   kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
 }
 

@@ -8,8 +8,11 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <stdexcept>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "stencil.cuh"
 
@@ -49,6 +52,67 @@ void stream_destroy(Stream s);                   // after synchronising it
 void sync_quiet(Stream s);                       // synchronise, ignoring errors
 }  // namespace dev
 
+// ------------------------------------------------------------------ device-controlled Krylov loops
+// State of one (F)GMRES solver kept in device memory, so that an Arnoldi step,
+// its convergence test and the decision to run another step need no host
+// round trip (and can run inside a captured CUDA graph).
+namespace kry {
+enum Status { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, NONFINITE = 3, LIMIT = 4 };
+struct Ctl {
+  int j;           // Arnoldi steps done in the current cycle (= index of the next column)
+  int m;           // cycle length
+  int status;      // Status
+  int k;           // columns of the last least-squares solve
+  int base;        // steps of the earlier cycles of the current linear solve
+  int cap;         // steps allowed per linear solve
+  long long total; // steps since the workspace was made (statistics)
+  double beta;     // residual norm at the start of the cycle
+  double tol;      // absolute stopping tolerance of the linear solve
+  double res;      // residual estimate |g_{j}|
+  double pad[3];
+};
+}  // namespace kry
+// Condition of a graph's WHILE node (a cudaGraphConditionalHandle); `on` is
+// false when the loop runs eagerly, without a graph.
+struct CondHandle {
+  unsigned long long h = 0;
+  bool on = false;
+};
+
+namespace dev {
+// A loop whose trip count the device decides.  prologue(s, h) enqueues the
+// work before the loop and must set ctl->status (and, when h.on, the loop
+// condition h); body(s, h, j) enqueues one iteration whose last kernel sets
+// both.  When stream st is being captured into a CUDA graph, the loop becomes
+// a WHILE conditional node of that graph (the body is captured once into the
+// node's body graph, on a helper stream of this thread, with j = -1);
+// otherwise the body is enqueued eagerly while ctl->status reads RUNNING (one
+// device-to-host read per iteration; j = ctl->j as read).  Returns the kernel
+// launches of one body iteration.
+long long device_while(Stream st, const kry::Ctl* ctl, const std::function<void(Stream, CondHandle)>& prologue,
+                       const std::function<void(Stream, CondHandle, int)>& body);
+bool capturing(Stream st);
+// Read the control block (device-to-host copy and stream synchronisation).
+void read_ctl(const kry::Ctl* ctl, kry::Ctl* out, Stream st);
+
+// One instantiated CUDA graph made by capturing `enqueue` on a private stream.
+struct Graph {
+  void* exec = nullptr;      // cudaGraphExec_t
+  void* graph = nullptr;     // cudaGraph_t
+  long long static_launches = 0;                      // kernel launches outside loops
+  // per loop, in capture order: its control block and the launches of one
+  // iteration outside nested loops
+  std::vector<std::pair<const kry::Ctl*, long long>> loops;
+  void capture(const std::function<void(Stream)>& enqueue);
+  void launch(Stream st);
+  // kernel launches of one run whose loops made iterations[i] iterations
+  long long executed(const std::vector<long long>& iterations) const;
+  void release();
+  bool ready() const { return exec != nullptr; }
+  ~Graph() { release(); }
+};
+}  // namespace dev
+
 // ------------------------------------------------------------------ kernel timing
 // Opt-in device-time accounting: when enabled, instrumented launchers bracket
 // their launch with CUDA events on the launching stream; dev::sync() harvests
@@ -75,6 +139,10 @@ extern std::atomic<long long> n_launch;  // kernel launches since load (every la
 // Timing is per process and single-stream: threads that drive concurrent
 // solves (ot_ipm_solve_batched) set `suspended` and are never timed.
 extern thread_local bool suspended;
+// Set while this thread captures a CUDA graph: no event pairs are recorded
+// (a captured launch has no per-launch events).
+extern thread_local bool capturing;
+extern thread_local long long t_captured;  // launches this thread has captured into graphs
 extern int stride;          // time one launch in `stride` of each enabled group
 void begin(int id, Stream s);
 void end(int id, Stream s, double bytes);
@@ -106,6 +174,49 @@ void k_scale_by_inv_norm(const double* x, const double* nrm2, double* y, i64 n, 
 void k_scale(const double* x, double a, double* y, i64 n, Stream s);
 void k_fill(double* x, double v, i64 n, Stream s);
 size_t k_reduce_scratch(int nv);  // doubles needed by `partial`
+
+// ------------------------------------------------------------------ device-controlled Arnoldi steps
+// The vector counts of these kernels are read from the control block (nv =
+// ctl->j + add) and their grids depend only on the basis size mmax, so one
+// capture serves every step.  Coefficients and norms are double; T is the
+// basis precision (double, or float for the inner Schur solve).
+size_t kry_partial_doubles(int mmax);  // scratch doubles of kry_dot / kry_update
+// out[v] = <V_v, w>, v < nv.
+// nv_hint: nv when the host knows it (eager loops; kernel-timing bytes only), else -1.
+template <typename T>
+void kry_dot(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const T* w, i64 n, double* out,
+             double* partial, int nv_hint, Stream s);
+// w -= sum_{v < nv} h[v] V_v; w32 (nullable) receives the new w in float;
+// norm_out (nullable): norm_out[nv] = |new w|^2.
+template <typename T>
+void kry_update(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, T* w, i64 n,
+                float* w32, double* norm_out, double* partial, int nv_hint, Stream s);
+// V_{j+1} = w / sqrt(nrm2[j+1]), j = ctl->j; V32 (nullable) and copy (nullable) receive it too.
+template <typename T>
+void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, T* V, i64 ld, float* V32, T* copy, i64 n,
+                    Stream s);
+// V0 = r / sqrt(nrm2[0]); V32_0 (nullable) and copy (nullable) receive it too.
+template <typename T>
+void kry_start_basis(const T* r, const double* nrm2, T* V0, float* V32_0, T* copy, i64 n, Stream s);
+// base[(ctl->j + add) * ld + i] = src[i]
+template <typename T>
+void kry_to_slot(const T* src, T* base, i64 ld, const kry::Ctl* ctl, int add, i64 n, Stream s);
+// Once per linear solve: base = 0, cap, tol = tol_rel * sqrt(sum_{i < nref} ref[i]) (nref > 0).
+void kry_solve_init(kry::Ctl* ctl, const double* ref, int nref, double tol_rel, int cap, Stream s);
+// Start of a cycle: beta = sqrt(nrm2[0]), g[0] = beta, j = 0; with tol_rel > 0 the
+// tolerance becomes tol_rel * beta; status RUNNING unless beta is already small
+// enough (or not finite); the loop condition h (if any) follows the status.
+void kry_start(kry::Ctl* ctl, const double* nrm2, int m, double tol_rel, double* g, CondHandle h, Stream s);
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes (hc1
+// nullable), Givens rotations, residual estimate, status, j += 1, condition.
+void kry_givens(kry::Ctl* ctl, const double* hc1, const double* hc2, double* H, int ldh, double* cs, double* sn,
+                double* g, CondHandle h, Stream s);
+// y = R^{-1} g over the ctl->j columns (ctl->k = j, ctl->base += j).
+void kry_backsolve(kry::Ctl* ctl, const double* H, int ldh, const double* g, double* y, Stream s);
+// x += sum_{v < ctl->k} y[v] Z_v
+template <typename T>
+void kry_combine(const T* Z, i64 ld, const kry::Ctl* ctl, int mmax, const double* y, T* x, i64 n, int nv_hint,
+                 Stream s);
 
 // FP32 overloads (mixed precision: the preconditioner's inner Krylov solve).
 // Per-thread accumulation is in float; cross-thread reductions and the
@@ -242,6 +353,10 @@ void k_mg_coarse_solve(int S, const LevelView<T>& L, int sweeps, T* line_c, T* l
 template <typename T>
 void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int nuc, T* line_c, T* line_r, T* agg,
                       Stream st);
+// Grant the fused cycle's kernel the shared memory these levels need (once,
+// before any stream capture: a capture cannot change kernel attributes).
+template <typename T>
+void k_mg_prepare_lower_cycle(int S, const LevelView<T>* levels, int nlev);
 // Shared memory the fused cycle over these levels needs; it must stay <= kFusedSmemLimit.
 template <typename T>
 size_t k_mg_fused_smem(int S, const LevelView<T>* levels, int nlev);

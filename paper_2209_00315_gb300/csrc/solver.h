@@ -1,5 +1,8 @@
 // solver.h -- workspace and host orchestration of the IPM / FGMRES / BB path.
 #pragma once
+#include <map>
+#include <memory>
+#include <string>
 #include <vector>
 
 #include "../../include/ot.h"
@@ -33,16 +36,27 @@ struct KrylovT {
   T* V = nullptr;          // (mmax+1) x n
   T* Z = nullptr;          // mmax x n
   T* w = nullptr;          // n
+  T* in = nullptr;         // n: the newest basis vector, the preconditioner's input
+  T* zout = nullptr;       // n: the preconditioner's output, before it is stored in Z
   double* hc1 = nullptr;   // mmax+2
   double* hc2 = nullptr;   // mmax+2
-  double* y = nullptr;     // mmax
+  double* y = nullptr;     // mmax+2
   // FP32 shadow of V and w (shadow = true): the Gram-Schmidt dot products are
   // taken from them in FP32 (the first pass always, the second when the solve's
   // target allows); the coefficients are applied to the FP64 basis.
   float* V32 = nullptr;    // (mmax+1) x n
   float* w32 = nullptr;    // n
+  // device-side iteration state (k_krylov.cu)
+  kry::Ctl* ctl = nullptr;
+  double* H = nullptr;     // (mmax+1) x mmax, column-major, leading dimension mmax+1
+  double* cs = nullptr;    // mmax+1
+  double* sn = nullptr;    // mmax+1
+  double* g = nullptr;     // mmax+2
+  double* part = nullptr;  // kry_partial_doubles(mmax)
+  double* scal = nullptr;  // 8: [0] squared norm of the cycle's start vector
   void build(int m, i64 n, bool shadow = false);
   void release();
+  int ldh() const { return mmax + 1; }
 };
 typedef KrylovT<double> Krylov;
 
@@ -91,6 +105,8 @@ struct Workspace {
   // counters of the current call
   long long outer_iters = 0, inner_iters = 0, capped_solves = 0;
   int cur_restart = 0, cur_inner = 0;
+  // captured FGMRES cycles (one graph per configuration of the cycle)
+  std::map<std::string, std::unique_ptr<dev::Graph>> graphs;
 
   Workspace(int n, int K, int precision, const ot_options& opt);
   ~Workspace();
@@ -109,8 +125,11 @@ int effective_restart(const ot_options& opt, i64 ntot);
 void refresh_coefficients(Workspace& W, Stream st);
 // One BB preconditioner application (Sec. 4.3): out = P_BB^{-1} v, both of length ntot.
 void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st);
-// FGMRES on the projected system; x (ntot) receives the solution; returns the final residual estimate.
-double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, double tol_abs, Stream st);
+// FGMRES on the projected system; x (ntot) receives the solution; stops at a
+// residual estimate <= tol_rel * sqrt(sum_{i < nref} tol_ref[i]) (device
+// scalars, squared norms); returns the final residual estimate.
+double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, double tol_rel,
+              const double* tol_ref, int nref, Stream st);
 // Residual at the state in W for parameter mu; returns ||F|| (norms[0..2]: component norms).
 double residual_norm(Workspace& W, double mu, Stream st, double* norms);
 // Newton direction at the state in W; requires the residual of that state in W.F*.

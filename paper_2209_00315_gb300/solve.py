@@ -27,6 +27,10 @@ def main(argv=None):
     p.add_argument("--restart", type=int, default=None, help="FGMRES restart length")
     p.add_argument("--max-iter", type=int, default=None, help="FGMRES iteration cap per Newton step")
     p.add_argument("--mu-factor", type=float, default=None, help="barrier reduction per stage (default 0.2)")
+    p.add_argument("--graphs", type=int, choices=[0, 1], default=None,
+                   help="1: FGMRES cycles as captured CUDA graphs (default); 0: launches one by one")
+    p.add_argument("--gs-shadow", type=int, choices=[0, 1], default=None,
+                   help="1: Gram-Schmidt dots from the FP32 basis copy (default); 0: all FP64")
     a = p.parse_args(argv)
 
     from ot_inputs import config_densities
@@ -42,6 +46,10 @@ def main(argv=None):
         extra["fgmres_max_iter"] = a.max_iter
     if a.mu_factor is not None:
         extra["mu_factor"] = a.mu_factor
+    if a.graphs is not None:
+        extra["graphs"] = a.graphs
+    if a.gs_shadow is not None:
+        extra["gs_shadow"] = a.gs_shadow
     opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
     walls, res = [], None
     for _ in range(a.repeat):
@@ -56,7 +64,7 @@ def main(argv=None):
         "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"], "inner_iters": st["inner_iters"],
         "gap": st["gap"], "wall_s": walls, "kernel_launches": capi.ot_kernel_launches(),
         "fgmres_restart": opt.fgmres_restart, "fgmres_max_iter": opt.fgmres_max_iter,
-        "mu_factor": opt.mu_factor, "mu_final": st["mu"],
+        "mu_factor": opt.mu_factor, "mu_final": st["mu"], "graphs": opt.graphs, "gs_shadow": opt.gs_shadow,
     }))
 
 
