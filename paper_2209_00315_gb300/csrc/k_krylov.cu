@@ -32,18 +32,47 @@ static void cuda_ok(cudaError_t e, const char* where) {
   }
 }
 
-static constexpr int kDotBlocks = 304;  // 2 per SM: each block walks one contiguous chunk of rows
+static constexpr int kDotBlocks = 608;  // 4 per SM, each walks one contiguous chunk of rows
 static constexpr int kUpdBlocks = 608;  // 4 per SM
 static constexpr int kThreads = 256;
 
 size_t kry_partial_doubles(int mmax) { return (size_t)kDotBlocks * (size_t)(mmax + 2) + kUpdBlocks + 64; }
 
-__device__ __forceinline__ double kwarp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T kwarp_sum_t(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ double kwarp_sum(double v) { return kwarp_sum_t<double>(v); }
 
+// 16-byte vectors of T: four floats or two doubles per load.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+  typedef double2 type;
+  static constexpr int E = 2;
+  __device__ static double dot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+  __device__ static void unpack(const double2& v, double (&r)[2]) {
+    r[0] = v.x;
+    r[1] = v.y;
+  }
+  __device__ static double2 pack(const double (&r)[2]) { return make_double2(r[0], r[1]); }
+};
+template <>
+struct Vec16<float> {
+  typedef float4 type;
+  static constexpr int E = 4;
+  __device__ static float dot(const float4& a, const float4& b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+  __device__ static void unpack(const float4& v, float (&r)[4]) {
+    r[0] = v.x;
+    r[1] = v.y;
+    r[2] = v.z;
+    r[3] = v.w;
+  }
+  __device__ static float4 pack(const float (&r)[4]) { return make_float4(r[0], r[1], r[2], r[3]); }
+};
 template <typename T>
 struct Vec2;
 template <>
@@ -55,73 +84,58 @@ struct Vec2<float> {
   typedef float2 type;
 };
 
-// Contiguous chunk [p0, p1) of the np element pairs for this block.
+// Contiguous chunk [p0, p1) of np items for this block.
 __device__ __forceinline__ void block_chunk(i64 np, i64* p0, i64* p1) {
   const i64 per = (np + gridDim.x - 1) / gridDim.x;
   *p0 = blockIdx.x * per;
   *p1 = min(np, *p0 + per);
 }
 
+// Rows of 16-byte loads: every basis row start and w on a 16-byte boundary.
+static bool aligned16(const void* a, const void* b, i64 ld, size_t elem) {
+  return (((uintptr_t)a | (uintptr_t)b) % 16) == 0 && ((size_t)ld * elem) % 16 == 0;
+}
+
 // ------------------------------------------------------------------ dot products
-// partial[b * pstride + v] = this block's share of <V_v, w>, v < nv; groups of
-// eight vectors per sweep over the block's rows (w is re-read from L1/L2).
+// partial[b * pstride + v] = this block's share of <V_v, w>, v < nv.  Warp w of
+// the block takes vectors w, w + 8, ...; its lanes walk the block's chunk of
+// rows with four 16-byte loads of V_v (and of w, an L1 hit after the first
+// vector) in flight, sum in T and reduce across the warp in T (the cross-block
+// sums are double).  No block barrier.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_kry_dot_kernel(const T* __restrict__ V, i64 ld,
                                                              const kry::Ctl* __restrict__ ctl, int add,
-                                                             const T* __restrict__ w, i64 n, bool pairs,
+                                                             const T* __restrict__ w, i64 n, bool vec,
                                                              double* __restrict__ partial, int pstride) {
-  __shared__ double sm[8][kThreads / 32];
+  typedef Vec16<T> VT;
+  typedef typename VT::type V4;
+  constexpr int E = VT::E;
   const int nv = ctl->j + add;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  using V2 = typename Vec2<T>::type;
-  for (int v0 = 0; v0 < nv; v0 += 8) {
-    const int cnt = min(8, nv - v0);
-    const T* Vg = V + (i64)v0 * ld;
-    T acc[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = 0;
-    if (pairs) {
-      i64 p0, p1;
-      block_chunk(n / 2, &p0, &p1);
-      const V2* w2 = reinterpret_cast<const V2*>(w);
-      for (i64 q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
-        const V2 wv = w2[q];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < cnt) {
-            const V2 x = reinterpret_cast<const V2*>(Vg + (i64)u * ld)[q];
-            acc[u] += x.x * wv.x + x.y * wv.y;
-          }
-      }
-      if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        const T wl = w[n - 1];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < cnt) acc[u] += Vg[(i64)u * ld + n - 1] * wl;
-      }
-    } else {
-      i64 e0, e1;
-      block_chunk(n, &e0, &e1);
-      for (i64 i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-        const T wi = w[i];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < cnt) acc[u] += Vg[(i64)u * ld + i] * wi;
-      }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const i64 nq = vec ? n / E : 0;                  // 16-byte groups
+  i64 q0, q1;
+  block_chunk(nq, &q0, &q1);
+  i64 e0 = nq * E, e1 = n;                         // scalar rows: the tail (or all rows when !vec)
+  if (!vec) block_chunk(n, &e0, &e1);
+  else if (blockIdx.x != gridDim.x - 1) e0 = e1;   // the vector tail belongs to the last block
+  const V4* w4 = reinterpret_cast<const V4*>(w);
+  for (int v = wp; v < nv; v += nw) {
+    const T* xv = V + (i64)v * ld;
+    const V4* x4 = reinterpret_cast<const V4*>(xv);
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    i64 q = q0 + lane;
+    for (; q + 96 < q1; q += 128) {
+      const V4 x0 = x4[q], x1 = x4[q + 32], x2 = x4[q + 64], x3 = x4[q + 96];
+      const V4 y0 = w4[q], y1 = w4[q + 32], y2 = w4[q + 64], y3 = w4[q + 96];
+      a0 += VT::dot(x0, y0);
+      a1 += VT::dot(x1, y1);
+      a2 += VT::dot(x2, y2);
+      a3 += VT::dot(x3, y3);
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const double t = kwarp_sum((double)acc[u]);
-      if (lane == 0) sm[u][wp] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      double t = 0.0;
-#pragma unroll
-      for (int q = 0; q < kThreads / 32; ++q) t += sm[threadIdx.x][q];
-      partial[(i64)blockIdx.x * pstride + v0 + threadIdx.x] = t;
-    }
-    __syncthreads();
+    for (; q < q1; q += 32) a0 += VT::dot(x4[q], w4[q]);
+    for (i64 i = e0 + lane; i < e1; i += 32) a1 += xv[i] * w[i];
+    const T t = kwarp_sum_t<T>((a0 + a1) + (a2 + a3));
+    if (lane == 0) partial[(i64)blockIdx.x * pstride + v] = (double)t;
   }
 }
 
@@ -138,17 +152,13 @@ __global__ void k_kry_dot_finish_kernel(const double* __restrict__ partial, int 
   if (lane == 0) out[v] = t;
 }
 
-static bool aligned_pairs(const void* a, const void* b, i64 ld, size_t elem) {
-  return (((uintptr_t)a | (uintptr_t)b) % (2 * elem)) == 0 && (ld % 2) == 0;
-}
-
 template <typename T>
 void kry_dot(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const T* w, i64 n, double* out,
              double* partial, int nv_hint, Stream s) {
   prof::begin(prof::MDOT, s);
   const int pstride = mmax + 2;
-  launch(k_kry_dot_kernel<T>, kDotBlocks, kThreads, 0, cs(s), V, ld, ctl, add, w, n,
-         aligned_pairs(V, w, ld, sizeof(T)), partial, pstride);
+  launch(k_kry_dot_kernel<T>, kDotBlocks, kThreads, 0, cs(s), V, ld, ctl, add, w, n, aligned16(V, w, ld, sizeof(T)),
+         partial, pstride);
   const int warps = kThreads / 32;
   launch(k_kry_dot_finish_kernel, (pstride + warps - 1) / warps, kThreads, 0, cs(s), (const double*)partial,
          kDotBlocks, pstride, ctl, add, out);
@@ -157,73 +167,141 @@ void kry_dot(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const T
 }
 
 // ------------------------------------------------------------------ update
-// w -= sum_{v < nv} h[v] V_v over the block's rows; w32 (nullable) = float(new w);
-// partial[block] = this block's share of |new w|^2 when norm is set.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_kry_update_kernel(const T* __restrict__ V, i64 ld,
-                                                                const kry::Ctl* __restrict__ ctl, int add,
-                                                                const double* __restrict__ h, T* w, i64 n,
-                                                                bool pairs, float* w32, bool norm,
-                                                                double* __restrict__ partial) {
-  extern __shared__ __align__(16) unsigned char kry_smem[];
-  T* hs = reinterpret_cast<T*>(kry_smem);
+// Block share of |w|^2 into partial[block] (after the block's rows are done).
+__device__ __forceinline__ void block_norm_partial(double acc, double* partial) {
   __shared__ double sm[kThreads / 32];
-  const int nv = ctl->j + add;
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = (T)h[v];
-  __syncthreads();
-  T acc = 0;
-  using V2 = typename Vec2<T>::type;
-  if (pairs) {
-    i64 p0, p1;
-    block_chunk(n / 2, &p0, &p1);
-    V2* w2 = reinterpret_cast<V2*>(w);
-    for (i64 q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
-      V2 wv = w2[q];
-      int v = 0;
-      for (; v + 8 <= nv; v += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const V2 x = reinterpret_cast<const V2*>(V + (i64)(v + u) * ld)[q];
-          wv.x -= hs[v + u] * x.x;
-          wv.y -= hs[v + u] * x.y;
-        }
-      }
-      for (; v < nv; ++v) {
-        const V2 x = reinterpret_cast<const V2*>(V + (i64)v * ld)[q];
-        wv.x -= hs[v] * x.x;
-        wv.y -= hs[v] * x.y;
-      }
-      w2[q] = wv;
-      if (w32) reinterpret_cast<float2*>(w32)[q] = make_float2((float)wv.x, (float)wv.y);
-      acc += wv.x * wv.x + wv.y * wv.y;
-    }
-    if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-      T wi = w[n - 1];
-      for (int v = 0; v < nv; ++v) wi -= hs[v] * V[(i64)v * ld + n - 1];
-      w[n - 1] = wi;
-      if (w32) w32[n - 1] = (float)wi;
-      acc += wi * wi;
-    }
-  } else {
-    i64 e0, e1;
-    block_chunk(n, &e0, &e1);
-    for (i64 i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-      T wi = w[i];
-      for (int v = 0; v < nv; ++v) wi -= hs[v] * V[(i64)v * ld + i];
-      w[i] = wi;
-      if (w32) w32[i] = (float)wi;
-      acc += wi * wi;
-    }
-  }
-  if (!norm) return;
-  double a = kwarp_sum((double)acc);
+  const double a = kwarp_sum(acc);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) t += sm[q];
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q];
     partial[blockIdx.x] = t;
   }
+}
+
+// w -= sum_{v < nv} h[v] V_v over the block's rows, in T; w32 (nullable) =
+// float(new w); partial[block] = this block's share of |new w|^2 when norm is set.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_kry_update_kernel(const T* __restrict__ V, i64 ld,
+                                                                const kry::Ctl* __restrict__ ctl, int add,
+                                                                const double* __restrict__ h, T* w, i64 n,
+                                                                bool vec, float* w32, bool norm,
+                                                                double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char kry_smem[];
+  T* hs = reinterpret_cast<T*>(kry_smem);
+  typedef Vec16<T> VT;
+  typedef typename VT::type V4;
+  constexpr int E = VT::E;
+  const int nv = ctl->j + add;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = (T)h[v];
+  __syncthreads();
+  T acc = 0;
+  const i64 nq = vec ? n / E : 0;
+  i64 q0, q1;
+  block_chunk(nq, &q0, &q1);
+  i64 e0 = nq * E, e1 = n;
+  if (!vec) block_chunk(n, &e0, &e1);
+  else if (blockIdx.x != gridDim.x - 1) e0 = e1;
+  V4* w4 = reinterpret_cast<V4*>(w);
+  for (i64 q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    T r[E];
+    VT::unpack(w4[q], r);
+    int v = 0;
+    for (; v + 8 <= nv; v += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        T x[E];
+        VT::unpack(reinterpret_cast<const V4*>(V + (i64)(v + u) * ld)[q], x);
+#pragma unroll
+        for (int e = 0; e < E; ++e) r[e] -= hs[v + u] * x[e];
+      }
+    }
+    for (; v < nv; ++v) {
+      T x[E];
+      VT::unpack(reinterpret_cast<const V4*>(V + (i64)v * ld)[q], x);
+#pragma unroll
+      for (int e = 0; e < E; ++e) r[e] -= hs[v] * x[e];
+    }
+    w4[q] = VT::pack(r);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (w32) w32[q * E + e] = (float)r[e];
+      acc += r[e] * r[e];
+    }
+  }
+  for (i64 i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+    T wi = w[i];
+    for (int v = 0; v < nv; ++v) wi -= hs[v] * V[(i64)v * ld + i];
+    w[i] = wi;
+    if (w32) w32[i] = (float)wi;
+    acc += wi * wi;
+  }
+  if (norm) block_norm_partial((double)acc, partial);
+}
+
+// The same update applied to an FP64 w from the FP32 copy of the basis, the
+// combination sum_v h[v] V32_v formed in FP32: for the second Gram-Schmidt
+// pass, whose coefficients are ~1e-7 of |w|, so that the FP32 rounding of the
+// correction is ~1e-14 of |w| (FP64 level).  Reads 4 bytes per basis entry
+// instead of 8 and keeps the FP64 units out of the loop.
+__global__ void __launch_bounds__(kThreads) k_kry_update_shadow_kernel(const float* __restrict__ V, i64 ld,
+                                                                       const kry::Ctl* __restrict__ ctl, int add,
+                                                                       const double* __restrict__ h, double* w,
+                                                                       i64 n, bool vec, bool norm,
+                                                                       double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char kry_smem[];
+  float* hs = reinterpret_cast<float*>(kry_smem);
+  const int nv = ctl->j + add;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = (float)h[v];
+  __syncthreads();
+  double acc = 0.0;
+  const i64 nq = vec ? n / 4 : 0;
+  i64 q0, q1;
+  block_chunk(nq, &q0, &q1);
+  i64 e0 = nq * 4, e1 = n;
+  if (!vec) block_chunk(n, &e0, &e1);
+  else if (blockIdx.x != gridDim.x - 1) e0 = e1;
+  for (i64 q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    int v = 0;
+    for (; v + 8 <= nv; v += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 x = reinterpret_cast<const float4*>(V + (i64)(v + u) * ld)[q];
+        const float hv = hs[v + u];
+        c.x += hv * x.x;
+        c.y += hv * x.y;
+        c.z += hv * x.z;
+        c.w += hv * x.w;
+      }
+    }
+    for (; v < nv; ++v) {
+      const float4 x = reinterpret_cast<const float4*>(V + (i64)v * ld)[q];
+      const float hv = hs[v];
+      c.x += hv * x.x;
+      c.y += hv * x.y;
+      c.z += hv * x.z;
+      c.w += hv * x.w;
+    }
+    double2* w2 = reinterpret_cast<double2*>(w) + 2 * q;
+    double2 a = w2[0], b = w2[1];
+    a.x -= (double)c.x;
+    a.y -= (double)c.y;
+    b.x -= (double)c.z;
+    b.y -= (double)c.w;
+    w2[0] = a;
+    w2[1] = b;
+    acc += a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
+  }
+  for (i64 i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+    float c = 0.f;
+    for (int v = 0; v < nv; ++v) c += hs[v] * V[(i64)v * ld + i];
+    const double wi = w[i] - (double)c;
+    w[i] = wi;
+    acc += wi * wi;
+  }
+  if (norm) block_norm_partial(acc, partial);
 }
 
 // out[nv] = sum of the blocks' |w|^2 shares (one block, fixed order).
@@ -247,14 +325,27 @@ void kry_update(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, cons
                 float* w32, double* norm_out, double* partial, int nv_hint, Stream s) {
   prof::begin(prof::MUPDATE, s);
   const size_t smem = sizeof(T) * (size_t)(mmax + 2);
-  const bool pairs = aligned_pairs(V, w, ld, sizeof(T)) && ((uintptr_t)w32 % 8) == 0;
+  const bool vec = aligned16(V, w, ld, sizeof(T));
   double* np = partial + (size_t)kDotBlocks * (size_t)(mmax + 2);
-  launch(k_kry_update_kernel<T>, kUpdBlocks, kThreads, smem, cs(s), V, ld, ctl, add, h, w, n, pairs, w32,
+  launch(k_kry_update_kernel<T>, kUpdBlocks, kThreads, smem, cs(s), V, ld, ctl, add, h, w, n, vec, w32,
          norm_out != nullptr, np);
   if (norm_out) launch(k_kry_norm_finish_kernel, 1, kThreads, 0, cs(s), (const double*)np, kUpdBlocks, ctl, add, norm_out);
   // the nv basis vectors and w read, w (and its FP32 copy) written
   prof::end(prof::MUPDATE, s,
             nv_hint >= 0 ? (double)sizeof(T) * (nv_hint + 2.0) * (double)n + (w32 ? 4.0 * (double)n : 0.0) : 0.0);
+}
+
+void kry_update_shadow(const float* V32, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, double* w,
+                       i64 n, double* norm_out, double* partial, int nv_hint, Stream s) {
+  prof::begin(prof::MUPDATE, s);
+  const size_t smem = sizeof(float) * (size_t)(mmax + 2);
+  const bool vec = aligned16(V32, w, ld, sizeof(float)) && ((uintptr_t)w % 32) == 0;
+  double* np = partial + (size_t)kDotBlocks * (size_t)(mmax + 2);
+  launch(k_kry_update_shadow_kernel, kUpdBlocks, kThreads, smem, cs(s), V32, ld, ctl, add, h, w, n, vec,
+         norm_out != nullptr, np);
+  if (norm_out) launch(k_kry_norm_finish_kernel, 1, kThreads, 0, cs(s), (const double*)np, kUpdBlocks, ctl, add, norm_out);
+  // the nv FP32 basis vectors read, w read and written
+  prof::end(prof::MUPDATE, s, nv_hint >= 0 ? 4.0 * nv_hint * (double)n + 16.0 * (double)n : 0.0);
 }
 
 // ------------------------------------------------------------------ basis vectors
@@ -483,8 +574,9 @@ template <typename T>
 void kry_combine(const T* Z, i64 ld, const kry::Ctl* ctl, int mmax, const double* y, T* x, i64 n, int nv_hint,
                  Stream s) {
   prof::begin(prof::MCOMBINE, s);
+  const bool pairs = (((uintptr_t)Z | (uintptr_t)x) % (2 * sizeof(T))) == 0 && (ld % 2) == 0;
   launch(k_kry_combine_kernel<T>, kUpdBlocks, kThreads, sizeof(T) * (size_t)(mmax + 2), cs(s), Z, ld, ctl, y, x, n,
-         aligned_pairs(Z, x, ld, sizeof(T)));
+         pairs);
   prof::end(prof::MCOMBINE, s, nv_hint >= 0 ? (double)sizeof(T) * (nv_hint + 2.0) * (double)n : 0.0);
 }
 

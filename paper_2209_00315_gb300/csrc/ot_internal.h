@@ -191,6 +191,11 @@ void kry_dot(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const T
 template <typename T>
 void kry_update(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, T* w, i64 n,
                 float* w32, double* norm_out, double* partial, int nv_hint, Stream s);
+// The same update of an FP64 w from an FP32 basis (the FP32 copy of V), the
+// combination formed in FP32: for the second Gram-Schmidt pass, whose
+// coefficients are ~1e-7 of |w|.
+void kry_update_shadow(const float* V32, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, double* w,
+                       i64 n, double* norm_out, double* partial, int nv_hint, Stream s);
 // V_{j+1} = w / sqrt(nrm2[j+1]), j = ctl->j; V32 (nullable) and copy (nullable) receive it too.
 template <typename T>
 void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, T* V, i64 ld, float* V32, T* copy, i64 n,

@@ -358,7 +358,10 @@ using OpFn = std::function<void(const T*, T*, Stream)>;
 // A Z = V H holds to FP64 rounding whichever precision computed them.
 // Second-pass coefficients from the shadow limit the orthogonality of V to
 // ~1e-7, which moves the residual estimate by that relative amount: harmless
-// for a target of 1e-5, so fgmres() asks for it only for targets >= 1e-8.
+// for a target of 1e-5, so fgmres() asks for it only for targets >= 1e-8.  In
+// that mode the second pass is applied from the shadow too, its combination
+// formed in FP32: those coefficients are ~1e-7 of |w|, so the FP32 rounding of
+// the correction (and of the coefficients H records) is ~1e-14 of |w|.
 template <typename T>
 static void arnoldi_step(KrylovT<T>& K, const OpFn<T>& prec, const OpFn<T>& op, bool shadow, bool fp32_reorth,
                          Stream st, CondHandle h, int j) {
@@ -373,18 +376,21 @@ static void arnoldi_step(KrylovT<T>& K, const OpFn<T>& prec, const OpFn<T>& op, 
     k_convert(reinterpret_cast<const double*>(K.w), K.w32, n, 1.0, st);
     kry_dot<float>(K.V32, n, K.ctl, 1, K.mmax, K.w32, n, K.hc1, K.part, nv, st);
     if (fp32_reorth) {
+      // second pass entirely from the shadow: dots, and the update formed in FP32
       kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc1, K.w, n, K.w32, nullptr, K.part, nv, st);
       kry_dot<float>(K.V32, n, K.ctl, 1, K.mmax, K.w32, n, K.hc2, K.part, nv, st);
+      kry_update_shadow(K.V32, n, K.ctl, 1, K.mmax, K.hc2, reinterpret_cast<double*>(K.w), n, K.hc2, K.part, nv, st);
     } else {
       kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc1, K.w, n, nullptr, nullptr, K.part, nv, st);
       kry_dot<T>(K.V, n, K.ctl, 1, K.mmax, K.w, n, K.hc2, K.part, nv, st);
+      kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st);
     }
   } else {
     kry_dot<T>(K.V, n, K.ctl, 1, K.mmax, K.w, n, K.hc1, K.part, nv, st);
     kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc1, K.w, n, nullptr, nullptr, K.part, nv, st);
     kry_dot<T>(K.V, n, K.ctl, 1, K.mmax, K.w, n, K.hc2, K.part, nv, st);
+    kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st);
   }
-  kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st);
   kry_next_basis<T>(K.w, K.hc2, K.ctl, K.V, n, shadow ? K.V32 : nullptr, K.in, n, st);
   kry_givens(K.ctl, K.hc1, K.hc2, K.H, K.ldh(), K.cs, K.sn, K.g, h, st);
 }
