@@ -31,7 +31,6 @@ WORKLOAD = "mix64"
 WORKLOAD_DESC = ("64x64 squares -> 8192 coarse / 32768 fine triangles, K=32, 3-Gaussian mixtures "
                  "(centres U[0.15,0.85]^2, sigma U[0.05,0.15], weights U[0.5,1.5], seeds 2/3), floor 1e-4, "
                  "unit mass, mu0=1, mu <- mu/5, stop at duality gap 1e-6")
-SAMPLE_N, SAMPLE_K = 12, 6   # bounded sample of the same density recipe for the CPU oracle
 SAMPLE_EVERY = 16            # time one launch in 16 of the roofline kernel inside the timed region
 METRIC = "IPM time-to-solution at duality gap 1e-6"
 WORKLOAD_N, WORKLOAD_K = 64, 32
@@ -44,10 +43,8 @@ def workload_config(args, world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "precision": args.precision, "n": n, "K": K,
             "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
             "unknowns": (K + 1) * 8 * n * n + K * 2 * n * n}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, by kernel group, from an ncu capture of the
-# kernel as it is built now; a group without an entry reports traffic None.  schur_line_smooth has none:
-# its capture (profiles/k_line_pcr_tile_mix64.md, 1.372 MB per launch) predates the move of
-# k_line_pcr_tile_kernel's body into inlined stage functions.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, keyed by (workload, kernel group), from an
+# ncu capture of the kernels as they are built now; a group without an entry reports traffic None.
 NCU_TRAFFIC: dict = {}
 
 
@@ -62,6 +59,7 @@ def parse_args():
     p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched solve")
     p.add_argument("--batched-streams", type=int, default=16)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-stress", action="store_true", help="skip the 256x256, K=64 roofline leg")
     return p.parse_args()
 
 
@@ -145,36 +143,80 @@ def summarise_clocks(lines) -> dict | None:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample_seconds() -> tuple[float, str]:
-    """Time the oracle (single thread) on the bounded sample; runs in a child process."""
-    code = ("import time,sys; sys.path.insert(0, %r)\n"
+# One exact (sparse-LU) Newton step of the oracle at the full 64x64, K = 32 size takes far longer than
+# a bounded benchmark sample allows, so the oracle runs the same code path on the same density recipe
+# at two smaller sizes, times its first Newton steps there, and the per-step time is carried to the
+# workload's unknown count with the growth exponent those two sizes show, times the Newton steps of
+# the solve: an extrapolation, labelled as such.
+ORACLE_SAMPLES = [(16, 2), (24, 2)]   # (squares per side n, Newton steps timed); K = n/2 as in the workload
+REFERENCE_SAMPLES = [(16, 1), (24, 1)]  # one Newton step per size for each step of the reference arm
+WORKLOAD_NEWTON_STEPS = 49            # Newton steps of the GPU solve of this workload (same mu schedule)
+
+
+def unknowns(n: int, K: int) -> int:
+    """Unknowns of the oracle's Newton system: phi ((K+1) N), rho and s (K N' each)."""
+    return (K + 1) * 8 * n * n + 2 * K * 2 * n * n
+
+
+def oracle_newton_seconds(threads: int, samples=ORACLE_SAMPLES) -> list:
+    """[(n, K, seconds per Newton step)] of the oracle's exact Newton steps at the sample sizes,
+    timed in a child process limited to `threads` BLAS threads."""
+    code = ("import time,sys,json; sys.path.insert(0, %r)\n"
             "from oracle import ipm\nfrom ot_inputs import config_densities\n"
-            "n,K,r0,r1 = config_densities('mixN', %d)\n"
-            "d = ipm.discretise(n, %d)\nt = time.perf_counter()\nr = ipm.ipm_solve(d, r0, r1)\n"
-            "print(time.perf_counter() - t, r.newton_steps)\n") % (ROOT, SAMPLE_N, SAMPLE_K)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+            "out = []\n"
+            "for n, steps in %r:\n"
+            "    n, K, r0, r1 = config_densities('mixN', n)\n"
+            "    d = ipm.discretise(n, K)\n"
+            "    phi, rho, s = ipm.initial_point(d, r0, r1, 1.0)\n"
+            "    t = time.perf_counter()\n"
+            "    for _ in range(steps):\n"
+            "        dphi, drho, ds, _ = ipm.newton_direction(d, phi, rho, s, r0, r1, 1.0)\n"
+            "        a = min(ipm.step_length(rho, drho, 0.99), ipm.step_length(s, ds, 0.99))\n"
+            "        phi, rho, s = phi + a * dphi, ipm.renormalise(d, rho + a * drho, r0), s + a * ds\n"
+            "    out.append((n, K, (time.perf_counter() - t) / steps))\n"
+            "print(json.dumps(out))\n") % (ROOT, list(samples))
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    sec, steps = out.stdout.split()[-2:]
-    desc = (f"oracle IPM (scipy SuperLU Newton solves, 1 thread) on the same density recipe at "
-            f"{SAMPLE_N}x{SAMPLE_N} squares, K={SAMPLE_K} ({steps} Newton steps), one full solve; not extrapolated")
-    return float(sec), desc
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_baseline(threads: int, newton_steps: int = WORKLOAD_NEWTON_STEPS, samples=ORACLE_SAMPLES) -> dict:
+    """Extrapolated oracle time to solution of the workload from the sample sizes."""
+    pts = oracle_newton_seconds(threads, samples)
+    (n1, k1, t1), (n2, k2, t2) = pts[0], pts[-1]
+    u1, u2, uw = unknowns(n1, k1), unknowns(n2, k2), unknowns(WORKLOAD_N, WORKLOAD_K)
+    import math
+
+    p = math.log(t2 / t1) / math.log(u2 / u1)
+    per_step = t2 * (uw / u2) ** p
+    sample = (f"oracle IPM (exact sparse-LU Newton steps, as it stands) on the workload's density recipe "
+              f"(3-Gaussian mixtures, seeds 2/3, floor 1e-4) at "
+              + ", ".join(f"{n}x{n}, K={k}: {t:.3f} s per Newton step" for n, k, t in pts)
+              + f"; per-step time grows as unknowns^{p:.2f}; extrapolated to 64x64, K=32 "
+                f"({uw} unknowns): {per_step:.1f} s per Newton step x {newton_steps} Newton steps")
+    import platform
+    return {"value": per_step * newton_steps, "unit": "s", "cores": threads, "kind": "oracle",
+            "extrapolated": True, "sample": sample, "per_newton_step_s": per_step, "growth_exponent": p,
+            "sample_points": pts, "cpu": platform.processor() or platform.machine(), "host_cores": os.cpu_count()}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    times = []
-    desc = ""
+    vals, base = [], None
     for i in range(args.warmup + args.steps):
-        t, desc = oracle_sample_seconds()
+        b = oracle_baseline(1, samples=REFERENCE_SAMPLES)
         if i >= args.warmup:
-            times.append(t)
-    v = sum(times) / len(times)
+            vals.append(b["value"])
+            base = b
+    v = sum(vals) / len(vals)
+    allc = oracle_baseline(os.cpu_count() or 1, samples=REFERENCE_SAMPLES)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, world),
-            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": dict(base, value=v), "cpu_baseline_all_cores": allc,
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -206,13 +248,10 @@ def run_ours(args, world, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_solves(precision, steps, warmup, groups=None):
-        opt = capi.default_options(precision=precision)
+    def timed_solves(steps, warmup, opt):
         for _ in range(warmup):
             capi.ot_ipm_solve(mesh, r0d, r1d, K, options=opt)
         barrier()
-        if groups is not None:
-            capi.ot_kernel_timing_enable(groups, sample_every=SAMPLE_EVERY)
         launches0 = capi.ot_kernel_launches()
         ms, res = [], None
         for _ in range(steps):
@@ -224,14 +263,11 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         barrier()
-        launches = capi.ot_kernel_launches() - launches0
-        timing = capi.ot_kernel_timing_read() if groups is not None else None
-        if groups is not None:
-            capi.ot_kernel_timing_enable(False)
-        return ms, res, launches, timing
+        return ms, res, capi.ot_kernel_launches() - launches0
 
-    # 1. which kernel group dominates (one untimed profiled solve, all groups on; per-launch
-    #    events need the launches issued one by one, so this solve runs without graphs)
+    # 1. kernel groups: one solve with CUDA events around every launch of every group.  Events
+    #    cannot bracket single kernels inside a graph, so this solve issues the same kernels one
+    #    by one (graphs = 0); each group's events then also hold the launch gap before its kernel.
     eager = capi.default_options(precision=args.precision, graphs=0)
     capi.ot_ipm_solve(mesh, r0d, r1d, K, options=eager)
     capi.ot_kernel_timing_enable(True)
@@ -241,9 +277,10 @@ def run_ours(args, world, rank, local):
     capi.ot_kernel_timing_enable(False)
     dominant = max(prof_all, key=lambda k: prof_all[k][0])
 
-    # 2. the timed region: only the dominant group carries events
+    # 2. the timed region: the default path (each FGMRES cycle one CUDA graph)
+    opt_main = capi.default_options(precision=args.precision)
     clocks = ClockSampler(local)
-    ms, res, launches, timing = timed_solves(args.precision, args.steps, args.warmup, groups=[dominant])
+    ms, res, launches = timed_solves(args.steps, args.warmup, opt_main)
     clk = clocks.stop()
     total = sum(ms)
     total = max_over_ranks(total, world, dev)
@@ -254,7 +291,7 @@ def run_ours(args, world, rank, local):
     r1h = torch.from_numpy(r1).pin_memory()
     opt = capi.default_options(precision=args.precision)
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(max(1, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -265,28 +302,68 @@ def run_ours(args, world, rank, local):
     e2e_obj = {"value": sum(e2e) / len(e2e), "unit": "s", "h2d_bytes_per_step": 2 * mesh.n_coarse * 8,
                "d2h_bytes_per_step": (Np + 2 * Nr) * 8 + 8}
 
-    # 4. FP64 GPU path for the mixed-vs-FP64 comparison of the metric
-    fp64 = None
+    # 4. FP64 GPU paths for the mixed-vs-FP64 comparison of the metric: all-FP64 (every
+    #    Gram-Schmidt pass in FP64), and FP64 with Gram-Schmidt dot products from an FP32 basis copy
+    fp64 = fp64_shadow = None
     if not args.no_fp64 and args.precision == "mixed":
-        ms64, res64, _, _ = timed_solves("fp64", max(1, args.steps // 2 + 1), 1)
-        fp64 = {"value": sum(ms64) / len(ms64) / 1e3, "unit": "s", "steps": len(ms64),
-                "cost": res64["cost"], "newton_steps": res64["stats"]["newton_steps"],
-                "fgmres_iters": res64["stats"]["fgmres_iters"]}
+        for name, shadow in (("fp64", 0), ("fp64_shadow", 1)):
+            o64 = capi.default_options(precision="fp64", gs_shadow=shadow)
+            ms64, res64, _ = timed_solves(max(1, min(3, args.steps // 2 + 1)), 1, o64)
+            rec = {"value": sum(ms64) / len(ms64) / 1e3, "unit": "s", "steps": len(ms64), "gs_shadow": shadow,
+                   "cost": res64["cost"], "newton_steps": res64["stats"]["newton_steps"],
+                   "fgmres_iters": res64["stats"]["fgmres_iters"],
+                   "cost_rel_diff_vs_mixed": abs(res64["cost"] - res["cost"]) / abs(res64["cost"])}
+            if shadow:
+                fp64_shadow = rec
+            else:
+                fp64 = rec
 
-    # roofline of the dominant group, from the events of the timed region
+    # roofline of each kernel group, from the events of the profiled solve (1.)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    t_ms, t_n, t_b = timing[dominant]
-    achieved = (t_b / 1e9) / (t_ms / 1e3) if t_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dominant),
-                "launches": t_n, "avg_launch_us": 1e3 * t_ms / max(t_n, 1),
-                "algorithmic_bytes_per_launch": t_b / max(t_n, 1),
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
+    peak_source = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+
+    def group_roofline(prof, name):
+        t_ms, t_n, t_b = prof[name]
+        achieved = (t_b / 1e9) / (t_ms / 1e3) if t_ms > 0 else 0.0
+        return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((WORKLOAD, name)), "launches": t_n,
+                "avg_launch_us": 1e3 * t_ms / max(t_n, 1), "algorithmic_bytes_per_launch": t_b / max(t_n, 1),
+                "peak_source": peak_source}
+
+    roofline = group_roofline(prof_all, dominant)
+    roofline_groups = {g: {k: v for k, v in group_roofline(prof_all, g).items()
+                           if k in ("achieved", "frac", "avg_launch_us", "launches", "algorithmic_bytes_per_launch")}
+                       for g in sorted(prof_all, key=lambda g: -prof_all[g][0]) if prof_all[g][1] > 0}
+
+    # the stress workload (256x256 squares, K = 64): levels and Krylov vectors beyond the 129 MB L2;
+    # the first two barrier stages with events on every group (as in 1.)
+    stress = None
+    if not args.no_stress and rank == 0:
+        sn, sK, s0, s1 = config_densities("stress256")
+        smesh = capi.Mesh(sn)
+        s0d, s1d = torch.from_numpy(s0).to(dev), torch.from_numpy(s1).to(dev)
+        so = capi.default_options(precision=args.precision, graphs=0)
+        capi.ot_kernel_timing_enable(True)
+        t0 = time.perf_counter()
+        sres = capi.ot_ipm_solve(smesh, s0d, s1d, sK, tol=0.5, options=so)
+        torch.cuda.synchronize()
+        st_wall = time.perf_counter() - t0
+        sprof = capi.ot_kernel_timing_read()
+        capi.ot_kernel_timing_enable(False)
+        sdom = max(sprof, key=lambda k: sprof[k][0])
+        stress = {"workload": "256x256 squares, K=64, 5-Gaussian mixtures (seeds 9/10), floor 1e-6; "
+                              "first two barrier stages (mu = 1, 0.2), launches issued one by one with events",
+                  "seconds": st_wall, "newton_steps": sres["stats"]["newton_steps"],
+                  "roofline": dict(group_roofline(sprof, sdom), traffic=NCU_TRAFFIC.get(("stress256", sdom))),
+                  "groups": {g: {k: v for k, v in group_roofline(sprof, g).items()
+                                 if k in ("achieved", "frac", "avg_launch_us", "launches")}
+                             for g in sorted(sprof, key=lambda g: -sprof[g][0]) if sprof[g][1] > 0}}
+        del smesh
 
     # 5. the batched workload: 64 independent problems of uneven size on concurrent streams
     batched = None
@@ -301,11 +378,18 @@ def run_ours(args, world, rank, local):
                 bmeshes[n_] = capi.Mesh(n_)
             items.append((bmeshes[n_], torch.from_numpy(a_).to(dev), torch.from_numpy(b_).to(dev), K_))
         bopt = capi.default_options(precision=args.precision)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bout = capi.ot_ipm_solve_batched(items, options=bopt, n_streams=args.batched_streams, raise_on_error=False)
-        torch.cuda.synchronize()
-        tb = max_over_ranks(time.perf_counter() - t0, world, dev)
+
+        def run_batch(o, streams):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = capi.ot_ipm_solve_batched(items, options=o, n_streams=streams, raise_on_error=False)
+            torch.cuda.synchronize()
+            return out, max_over_ranks(time.perf_counter() - t0, world, dev)
+
+        bout, tb = run_batch(bopt, args.batched_streams)
+        # comparators: the same problems one after another on one stream, and the batch in FP64
+        _, t_seq = run_batch(bopt, 1)
+        bout64, t64 = run_batch(capi.default_options(precision="fp64"), args.batched_streams)
         failed = [i for i, o in enumerate(bout) if o["status"] != 0]
         batched = {"workload": "64 problems, side in {16,24,32,48,64}, K in {8,16,24,32}, 1-4 Gaussians, "
                                "floor 1e-4 (seeds 1000..1063)",
@@ -314,12 +398,13 @@ def run_ours(args, world, rank, local):
                    "problems_this_rank": len(items),
                    "failed": {i: capi.STATUS.get(bout[i]["status"], bout[i]["status"]) for i in failed},
                    "newton_steps": sum(o["stats"]["newton_steps"] for o in bout),
+                   "one_after_another_seconds": t_seq, "fp64_seconds": t64,
+                   "fp64_converged": sum(1 for o in bout64 if o["status"] == 0),
                    "unknowns": sum((K_ + 1) * 8 * n_ * n_ + K_ * 2 * n_ * n_ for n_, K_, _, _ in specs)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, desc = oracle_sample_seconds()
-        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = oracle_baseline(1, res["stats"]["newton_steps"])
 
     if rank != 0:
         return
@@ -335,11 +420,14 @@ def run_ours(args, world, rank, local):
         "result": {"cost": res["cost"], "newton_steps": st["newton_steps"], "fgmres_iters": st["fgmres_iters"],
                    "inner_iters": st["inner_iters"], "final_residual": st["final_residual"], "gap": st["gap"]},
         "fp64": fp64,
+        "fp64_shadow": fp64_shadow,
         "batched": batched,
         "speedup_mixed_vs_fp64": (fp64["value"] / sec) if fp64 else None,
         "e2e": e2e_obj,
         "gpu_launches": launches,
         "roofline": roofline,
+        "roofline_groups": roofline_groups,
+        "stress256": stress,
         "kernel_share_ms_per_solve": {k: v[0] for k, v in prof_all.items()},
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -1,6 +1,8 @@
 """Host logic of bench.py that needs no GPU: the summary of the nvidia-smi
 clock samples taken during the timed region, and the reference arm (the CPU
 oracle on its bounded sample) and its JSON line."""
+import numpy as np
+
 import bench
 
 
@@ -32,26 +34,40 @@ def _args(**kw):
 
 
 def test_reference_arm_prints_one_line_with_the_workload_config(monkeypatch, capsys):
-    """The reference arm times the oracle on its bounded sample (warm-up runs
-    discarded), prints one JSON line on rank 0 with the same metric, unit and config
-    as the GPU arm, and nothing on other ranks."""
+    """The reference arm times the oracle's Newton steps on its bounded samples (warm-up
+    runs discarded), extrapolates to the workload, prints one JSON line on rank 0 with
+    the same metric, unit and config as the GPU arm, and nothing on other ranks."""
     import json
 
-    times = iter([9.0, 2.0, 4.0])
-    monkeypatch.setattr(bench, "oracle_sample_seconds", lambda: (next(times), "a bounded sample"))
+    # per-step times (n=16, n=24) of three runs: warm-up, then two timed steps
+    runs = iter([[(16, 8, 9.0), (24, 12, 90.0)], [(16, 8, 1.0), (24, 12, 10.0)], [(16, 8, 1.0), (24, 12, 10.0)],
+                 [(16, 8, 0.5), (24, 12, 5.0)]])
+    monkeypatch.setattr(bench, "oracle_newton_seconds", lambda threads, samples=None: next(runs))
     bench.run_reference(_args(), 1, 0)
     line = json.loads(capsys.readouterr().out.strip())
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "s"
-    assert line["value"] == 3.0 and line["higher_is_better"] is False
+    assert line["higher_is_better"] is False
     assert line["config"] == bench.workload_config(_args(), 1)
-    assert line["cpu_baseline"] == {"value": 3.0, "unit": "s", "cores": 1, "kind": "oracle",
-                                    "sample": "a bounded sample"}
-    assert line["e2e"] == {"value": 3.0, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["extrapolated"] is True and cb["cores"] == 1
+    # per-step time 10 s at 24x24, K=12, growing as unknowns^p with 10x over the step from n=16
+    u16, u24, uw = bench.unknowns(16, 8), bench.unknowns(24, 12), bench.unknowns(64, 32)
+    p = np.log(10.0) / np.log(u24 / u16)
+    expect = 10.0 * (uw / u24) ** p * bench.WORKLOAD_NEWTON_STEPS
+    assert abs(line["value"] - expect) < 1e-9 * expect and abs(cb["value"] - expect) < 1e-9 * expect
+    assert "64x64, K=32" in cb["sample"] and "extrapolated" in cb["sample"]
+    assert line["cpu_baseline_all_cores"]["per_newton_step_s"] > 0
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     bench.run_reference(_args(), 2, 1)
     assert capsys.readouterr().out == ""
 
 
+def test_unknowns_of_the_newton_system():
+    """(K+1) N + 2 K N' with N = 8 n^2, N' = 2 n^2: 1,605,632 for 64x64, K = 32 (phi, rho and s)."""
+    assert bench.unknowns(64, 32) == 33 * 32768 + 2 * 32 * 8192 == 1605632
+
+
 def test_oracle_sample_runs_in_a_child_process():
-    """The child process that times the oracle sample finishes and reports its Newton steps."""
-    sec, desc = bench.oracle_sample_seconds()
-    assert 0 < sec < 600 and "Newton steps" in desc and f"{bench.SAMPLE_N}x{bench.SAMPLE_N}" in desc
+    """The child process that times the oracle's Newton steps finishes and reports each size."""
+    pts = bench.oracle_newton_seconds(1, samples=[(4, 1), (6, 1)])
+    assert [(n, K) for n, K, _ in pts] == [(4, 4), (6, 4)] and all(0 < t < 60 for _, _, t in pts)

@@ -101,6 +101,11 @@ MUTATIONS = {
     "R_T weighted by |e|/|w| instead of |e||w|": (
         "operators.py", "sp.diags(f.edge_dist * f.edge_len)", "sp.diags(f.edge_len / f.edge_dist)",
         "symmetric_saddle"),
+    "dual value's boundary kinetic terms weighted dt/2 instead of dt/4": (
+        "ipm.py", "return term - 0.25 * d.dt * corr", "return term - 0.5 * d.dt * corr", "identity_at_any_point"),
+    "cost without the 1/2 of the kinetic energy": (
+        "ipm.py", "total += 0.5 * float(np.dot(d.W * rt[k], g * g))", "total += float(np.dot(d.W * rt[k], g * g))",
+        "identity_at_any_point"),
     "adjoint: initial-time flux with the wrong sign": (
         "adjoint.py", "(MJ / d.dt + flux(0))", "(MJ / d.dt - flux(0))", "adjoint_gradient_matches"),
     "adjoint: final-time flux with the wrong sign": (

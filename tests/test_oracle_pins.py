@@ -615,6 +615,29 @@ def test_duality_gap_identity(converged_small):
     assert ipm.residual_norm(F) < 1e-12
 
 
+@pytest.mark.parametrize("graded", [False, True])
+def test_duality_gap_identity_at_any_point(graded):
+    """The gap identity off the solution, derived by summation by parts from the
+    definitions of F_phi, F_rho (time term J^T M, reading R3), the cost and the
+    dual value (reading R15), with R_T = R_E^T diag(|e||w|):
+      C - D - mu |Omega| K/(K+1) = dt [ sum_k phi^k.F_phi^k - sum_k rho^k.F_rho^k + sum_k |c'|.(F_s^k) ],
+    F_s = rho s - mu.  It holds at every (phi, rho, s), so a term dropped or
+    mis-weighted in the residual, the cost or the dual value breaks it; on the
+    graded grid |c'| differs from cell to cell."""
+    n, K = 3, 4
+    d = _graded_discretisation(n, K) if graded else ipm.discretise(n, K)
+    phi, rho, s, r0, r1 = _random_state(d, seed=11 + int(graded))
+    mu = 0.37
+    Fphi, Frho, Fs = ipm.residual(d, phi, rho, s, r0, r1, mu)
+    C = ipm.cost(d, phi, rho, r0, r1)
+    D = ipm.dual_value(d, phi, r0, r1)
+    area = d.t.coarse.area
+    rhs = d.dt * (phi @ Fphi - rho @ Frho + np.tile(area, K) @ Fs)
+    lhs = C - D - mu * area.sum() * K / (K + 1)
+    scale = abs(C) + abs(D) + d.dt * (abs(phi) @ abs(Fphi) + abs(rho) @ abs(Frho))
+    assert abs(lhs - rhs) < 1e-13 * scale, (lhs, rhs)
+
+
 def test_mass_positivity_complementarity(converged_small):
     """Remark one-mass: |c'|^T rho^k = |c'|^T rho^0; rho, s > 0; rho s = mu."""
     d, r0, r1, res = converged_small
@@ -764,3 +787,4 @@ def test_separable_densities_converge_to_quantile_w2():
         d = ipm.discretise(n, n)
         err[n] = ipm.ipm_solve(d, cell_average(n, c0, s0), cell_average(n, c1, s1)).cost / target - 1.0
     assert abs(err[8]) < abs(err[4]) < 0.15 and abs(err[8]) < 0.01, err
+
