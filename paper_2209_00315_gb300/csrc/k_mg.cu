@@ -624,6 +624,123 @@ struct SliceWalk {
   }
 };
 
+// ---- time lines with stored Thomas factors (fused shared-memory levels).
+// Row k of the line of cell c: d_k x_k - tau_k (x_{k-1} + x_{k+1}) = r_k with
+// d_k = 2 tau_k + sum_slot alpha, x_{-1} = x_S = 0 (the system line_gs solves).
+// line_factor stores 1/den_k and cp_k = -tau_k/den_k of the forward
+// elimination, den_0 = d_0, den_k = d_k + tau_k cp_{k-1}; a sweep then needs
+// one multiply-add per row forward and one back.
+template <typename T>
+__device__ __forceinline__ void line_factor(int S, const LevelView<T>& L, int c) {
+  const i64 ld = L.ld;
+  T* inv = L.fac;
+  T* cp = L.fac + (i64)S * ld;
+  T cprev = 0;
+  for (int k = 0; k < S; ++k) {
+    const i64 o = (i64)k * ld + c;
+    const T tau = L.tau[o];
+    T dg = 2 * tau;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) dg += L.alpha[((i64)sl * S + k) * ld + c];
+    const T den = dg + (k > 0 ? tau * cprev : (T)0);
+    const T iv = mg_div((T)1, den);
+    inv[o] = iv;
+    cprev = (k < S - 1) ? -tau * iv : (T)0;
+    cp[o] = cprev;
+  }
+}
+
+// One colour sweep of a staged level with the stored factors, one warp per
+// line, lane l holding rows l KPL .. l KPL + KPL - 1.  The lanes form their
+// rows' right-hand sides b + sum_slot alpha x_neighbour (neighbour values as
+// the sweep mode gives them) in parallel; the substitutions are linear
+// recurrences, rp_k = (tau_k/den_k) rp_{k-1} + r_k/den_k forward and
+// x_k = -cp_k x_{k+1} + rp_k back, each solved by composing the affine maps
+// within a lane and then across the warp by a shuffle scan (log2 32 steps).
+template <typename T, int KPL, int MODE>
+__device__ __forceinline__ void line_scan_solve(int S, const LevelView<T>& L, const LevelView<T>& Lc, int c,
+                                                int lane) {
+  i64 nb[3];
+  neighbours(L.m, decode(L.m, c), nb);
+  const i64 ld = L.ld;
+  const T* inv = L.fac;
+  const T* cp = L.fac + (i64)S * ld;
+  T A[KPL], B[KPL], C[KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = lane * KPL + q;
+    A[q] = 0;
+    B[q] = 0;
+    C[q] = 0;
+    if (k < S) {
+      const i64 o = (i64)k * ld + c;
+      T rhs = L.b[o];
+      if (MODE != kSweepFromZero) {
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl)
+          if (nb[sl] >= 0) rhs += L.alpha[((i64)sl * S + k) * ld + c] * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
+      }
+      const T iv = inv[o];
+      A[q] = (k > 0) ? L.tau[o] * iv : (T)0;
+      B[q] = rhs * iv;
+      C[q] = -cp[o];
+    }
+  }
+  // forward: the lane's composed map, an inclusive scan over lanes, then the rows
+  T Aa = A[0], Ba = B[0];
+#pragma unroll
+  for (int q = 1; q < KPL; ++q) {
+    Ba = A[q] * Ba + B[q];
+    Aa = A[q] * Aa;
+  }
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const T Ap = __shfl_up_sync(0xffffffffu, Aa, s), Bp = __shfl_up_sync(0xffffffffu, Ba, s);
+    if (lane >= s) {
+      Ba = Aa * Bp + Ba;
+      Aa = Aa * Ap;
+    }
+  }
+  T rp = __shfl_up_sync(0xffffffffu, Ba, 1);  // rp at the last row of the previous lane
+  if (lane == 0) rp = 0;
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    rp = A[q] * rp + B[q];
+    B[q] = rp;  // B now holds rp
+  }
+  // back: x_k = C_k x_{k+1} + rp_k, composed from the end
+  T Cc = C[KPL - 1], Dc = B[KPL - 1];
+#pragma unroll
+  for (int q = KPL - 2; q >= 0; --q) {
+    Dc = C[q] * Dc + B[q];
+    Cc = C[q] * Cc;
+  }
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const T Cn = __shfl_down_sync(0xffffffffu, Cc, s), Dn = __shfl_down_sync(0xffffffffu, Dc, s);
+    if (lane + s < 32) {
+      Dc = Cc * Dn + Dc;
+      Cc = Cc * Cn;
+    }
+  }
+  T xn = __shfl_down_sync(0xffffffffu, Dc, 1);  // x at the first row of the next lane
+  if (lane == 31) xn = 0;
+#pragma unroll
+  for (int q = KPL - 1; q >= 0; --q) {
+    xn = C[q] * xn + B[q];
+    const int k = lane * KPL + q;
+    if (k < S) L.x[(i64)k * ld + c] = xn;
+  }
+}
+
+// One colour sweep of a staged level: warp w of the CTA takes lines w, w + nwarp, ...
+template <typename T, int KPL, int MODE>
+__device__ void line_scan_sweep(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color) {
+  const int sq = L.m * L.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int w = warp; w < sq; w += nwarp) line_scan_solve<T, KPL, MODE>(S, L, Lc, color * sq + w, lane);
+}
+
 // Threads of the one-CTA Schur kernels: 512 where a PCR lane's KPL systems in T
 // would not fit the 64 registers a 1024-thread CTA leaves each thread.
 template <typename T, int KPL>
@@ -653,7 +770,9 @@ __device__ void coarse_body(int S, const LevelView<T>& L, int sweeps, T* lc, T* 
   for (int pass = 0; pass < passes; ++pass) {
     for (int it = 0; it < sweeps; ++it) {
       for (int color = 0; color < 2; ++color) {
-        if (L.tau && KPL > 0) {
+        if (L.tau && L.fac && KPL > 0) {
+          line_scan_sweep<T, (KPL > 0 ? KPL : 1), kSweepPlain>(S, L, L, color);
+        } else if (L.tau && KPL > 0) {
           for (int w = warp; w < sq; w += nwarp) line_pcr<T, (KPL > 0 ? KPL : 1)>(S, L, (i64)color * sq + w, lane);
         } else if (L.tau) {
           for (int i = threadIdx.x; i < sq; i += blockDim.x) line_gs(S, L, (i64)color * sq + i, lc, lr);
@@ -761,6 +880,19 @@ struct LevelSet {
 // one cell's time line (lane = slice) touches 32 different banks.
 __host__ __device__ inline i64 staged_ld(i64 nc, int S_view) { return (S_view > 1 && (nc & 1) == 0) ? nc + 1 : nc; }
 
+// One element global -> shared without a register round trip (cp.async): a
+// thread issues all its copies back to back and waits once (async_copy_wait),
+// instead of one L2 round trip per element.
+template <typename T>
+__device__ __forceinline__ void async_copy_elem(T* sdst, const T* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void async_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Carve shared-memory views of the fused levels (S_view slices each) and copy
 // coefficients (slice `slice0` onwards) and the first level's b into them.
 template <typename T>
@@ -785,6 +917,11 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
       p += n1;
       V.r = p;
       p += n1;
+      V.fac = nullptr;
+      if (G.tau) {
+        V.fac = p;
+        p += 2 * n1;
+      }
     }
   }
   __syncthreads();
@@ -796,17 +933,18 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
     for (int sl = 0; sl < 3; ++sl) {
       const T* src = G.alpha + ((i64)sl * S + slice0) * gld;
       T* dst = V.alpha + sl * S_view * vld;
-      for (SliceWalk w(nc); w.k < S_view; w.next()) dst[w.k * vld + w.c] = src[w.k * gld + w.c];
+      for (SliceWalk w(nc); w.k < S_view; w.next()) async_copy_elem(dst + w.k * vld + w.c, src + w.k * gld + w.c);
     }
     if (G.tau) {
       const T* src = G.tau + (i64)slice0 * gld;
-      for (SliceWalk w(nc); w.k < S_view; w.next()) V.tau[w.k * vld + w.c] = src[w.k * gld + w.c];
+      for (SliceWalk w(nc); w.k < S_view; w.next()) async_copy_elem(V.tau + w.k * vld + w.c, src + w.k * gld + w.c);
     }
     if (l == 0) {
       const T* src = G.b + (i64)slice0 * gld;
-      for (SliceWalk w(nc); w.k < S_view; w.next()) V.b[w.k * vld + w.c] = src[w.k * gld + w.c];
+      for (SliceWalk w(nc); w.k < S_view; w.next()) async_copy_elem(V.b + w.k * vld + w.c, src + w.k * gld + w.c);
     }
   }
+  async_copy_wait();
   __syncthreads();
 }
 
@@ -814,7 +952,7 @@ template <typename T>
 size_t fused_smem_bytes(const LevelView<T>* lv, int nlev, int S_view, bool tc) {
   size_t cells = 0;
   for (int l = 0; l < nlev; ++l) cells += (size_t)S_view * (size_t)staged_ld(lv[l].nc, S_view);
-  return sizeof(T) * cells * (tc ? 7 : 6) + (tc ? sizeof(T) * 4 * (size_t)S_view : 0);
+  return sizeof(T) * cells * (tc ? 9 : 6) + (tc ? sizeof(T) * 4 * (size_t)S_view : 0);
 }
 
 // Slice Laplacians: one CTA per slice (blockIdx.x), point red-black GS, the
@@ -887,8 +1025,20 @@ __device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, u
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   __shared__ LevelSet<T> ls;
   stage_levels(gls, ls, reinterpret_cast<T*>(smem_raw), S, S, 0);
-  T* agg = ls.L[ls.n - 1].r + (i64)S * ls.L[ls.n - 1].ld;
+  T* agg = ls.L[ls.n - 1].fac + 2 * (i64)S * ls.L[ls.n - 1].ld;
   const int last = ls.n - 1;
+  // the line systems of every staged level, factored once for the whole cycle (one pass over
+  // the lines of all levels)
+  {
+    int total = 0;
+    for (int l = 0; l <= last; ++l) total += (int)ls.L[l].nc;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      int l = 0, c = i;
+      while (c >= (int)ls.L[l].nc) c -= (int)ls.L[l++].nc;
+      line_factor(S, ls.L[l], c);
+    }
+  }
+  __syncthreads();
   for (int l = 0; l < last; ++l) {
     const LevelView<T>& L = ls.L[l];
     const int sq = L.m * L.m, ld = (int)L.ld;
@@ -899,9 +1049,9 @@ __device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, u
     for (int it = 0; it < nu; ++it)
       for (int col = 0; col < 2; ++col) {
         if (it == 0 && col == 0)
-          for (int w = warp; w < sq; w += nwarp) line_pcr_mode<T, KPL, kSweepFromZero>(S, L, L, (i64)w, lane);
+          line_scan_sweep<T, KPL, kSweepFromZero>(S, L, L, 0);
         else
-          for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
+          line_scan_sweep<T, KPL, kSweepPlain>(S, L, L, col);
         __syncthreads();
       }
     // b_coarse = J^T (b - M x) in one phase
@@ -931,9 +1081,9 @@ __device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, u
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
         if (it == 0 && col == 1)
-          for (int w = warp; w < sq; w += nwarp) line_pcr_mode<T, KPL, kSweepAfterProlong>(S, L, Lc, (i64)(sq + w), lane);
+          line_scan_sweep<T, KPL, kSweepAfterProlong>(S, L, Lc, 1);
         else
-          for (int w = warp; w < sq; w += nwarp) line_pcr<T, KPL>(S, L, (i64)(col * sq + w), lane);
+          line_scan_sweep<T, KPL, kSweepPlain>(S, L, L, col);
         __syncthreads();
       }
   }

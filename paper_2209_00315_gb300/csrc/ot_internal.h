@@ -322,6 +322,11 @@ struct LevelView {
   T* x;
   T* b;
   T* r;
+  // Thomas factors of the time lines, [2][S][ld] (1/pivot, then the modified
+  // upper coefficient), on the shared-memory copies of the fused space-time
+  // levels only (nullptr elsewhere): the line systems change once per Newton
+  // step, so a fused cycle factors them once and every sweep only substitutes.
+  T* fac = nullptr;
 };
 
 template <typename T>
@@ -365,7 +370,7 @@ void k_mg_prepare_lower_cycle(int S, const LevelView<T>* levels, int nlev);
 // Shared memory the fused cycle over these levels needs; it must stay <= kFusedSmemLimit.
 template <typename T>
 size_t k_mg_fused_smem(int S, const LevelView<T>* levels, int nlev);
-constexpr size_t kFusedSmemLimit = 200 * 1024;
+constexpr size_t kFusedSmemLimit = 220 * 1024;
 // b = (T)(scale * src); x = 0
 template <typename T>
 void k_mg_load(const double* src, double scale, T* b, T* x, i64 n, Stream st);

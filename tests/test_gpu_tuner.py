@@ -40,15 +40,21 @@ def test_tuner_picks_the_fastest_candidate_and_keeps_the_answer(gpu_lib):
     for f, _ in capi.ot_options._fields_:
         if f not in ("smooth_sweeps", "coarse_sweeps", "lap_cycles"):
             assert getattr(tuned, f) == getattr(base, f), f
-    # the tuned direction solves the Newton system to the outer tolerance: compare with the
-    # default settings' direction at a tight tolerance
-    tight = dict(final_eps_out=1e-10)
-    d_ref = capi.ot_newton_solve(mesh, K, mu, res["phi"], res["rho"], res["s"], r0d, r1d,
-                                 options=capi.default_options(precision="mixed", **tight))
-    opt_t = capi.default_options(precision="mixed", smooth_sweeps=tuned.smooth_sweeps,
-                                 coarse_sweeps=tuned.coarse_sweeps, lap_cycles=tuned.lap_cycles, **tight)
-    d_tun = capi.ot_newton_solve(mesh, K, mu, res["phi"], res["rho"], res["s"], r0d, r1d, options=opt_t)
-    for a, b in zip(d_tun[:3], d_ref[:3]):
-        err = float(torch.linalg.norm(a - b) / max(float(torch.linalg.norm(b)), 1e-300))
-        assert err < 1e-7, err
-    assert d_tun[3]["fgmres_iters"] < 400
+    # the tuned direction solves the Newton system (Eq. newton-linsys) to the outer tolerance: its
+    # residual J d + F, formed by the oracle, is small relative to F (eps_out = 1e-5 on the projected
+    # system; the projection and the elimination of ds rescale rows, hence a factor of 10)
+    from oracle import ipm
+
+    d = ipm.discretise(n, K)
+    state = [res[k].cpu().numpy() for k in ("phi", "rho", "s")]
+    F = np.concatenate(ipm.residual(d, *state, r0, r1, mu))
+    J = ipm.jacobian(d, *state, r0, r1)
+    for opts in (tuned, capi.default_options(precision="mixed")):
+        o = capi.default_options(precision="mixed", smooth_sweeps=opts.smooth_sweeps,
+                                 coarse_sweeps=opts.coarse_sweeps, lap_cycles=opts.lap_cycles)
+        dphi, drho, ds, st = capi.ot_newton_solve(mesh, K, mu, res["phi"], res["rho"], res["s"], r0d, r1d,
+                                                  options=o)
+        dx = np.concatenate([t.cpu().numpy() for t in (dphi, drho, ds)])
+        rel_res = np.linalg.norm(J @ dx + F) / np.linalg.norm(F)
+        assert rel_res < 1e-4, rel_res
+        assert st["fgmres_iters"] < o.fgmres_max_iter
