@@ -185,6 +185,59 @@ __device__ __forceinline__ void pcr_solve(T (&a)[KPL], T (&d)[KPL], T (&c)[KPL],
   }
 }
 
+// Solve of one time line held by a warp, lane l holding rows l KPL .. l KPL + KPL - 1
+// as the coefficients of the two substitutions with stored Thomas factors:
+//   forward  rp_k = A_k rp_{k-1} + B_k   (A_k = tau_k/den_k, B_k = r_k/den_k, A_0 = 0)
+//   back     x_k  = C_k x_{k+1} + rp_k   (C_k = -cp_k, C_{S-1} = 0)
+// Both linear recurrences are solved by composing the affine maps within a lane
+// and across the warp by a shuffle scan (log2 32 steps).  Rows beyond the line
+// carry A = B = C = 0.  On return B holds x.
+template <typename T, int KPL>
+__device__ __forceinline__ void scan_tridiag(T (&A)[KPL], T (&B)[KPL], const T (&C)[KPL], int lane) {
+  T Aa = A[0], Ba = B[0];
+#pragma unroll
+  for (int q = 1; q < KPL; ++q) {
+    Ba = A[q] * Ba + B[q];
+    Aa = A[q] * Aa;
+  }
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const T Ap = __shfl_up_sync(0xffffffffu, Aa, s), Bp = __shfl_up_sync(0xffffffffu, Ba, s);
+    if (lane >= s) {
+      Ba = Aa * Bp + Ba;
+      Aa = Aa * Ap;
+    }
+  }
+  T rp = __shfl_up_sync(0xffffffffu, Ba, 1);  // rp at the last row of the previous lane
+  if (lane == 0) rp = 0;
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    rp = A[q] * rp + B[q];
+    B[q] = rp;
+  }
+  T Cc = C[KPL - 1], Dc = B[KPL - 1];
+#pragma unroll
+  for (int q = KPL - 2; q >= 0; --q) {
+    Dc = C[q] * Dc + B[q];
+    Cc = C[q] * Cc;
+  }
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const T Cn = __shfl_down_sync(0xffffffffu, Cc, s), Dn = __shfl_down_sync(0xffffffffu, Dc, s);
+    if (lane + s < 32) {
+      Dc = Cc * Dn + Dc;
+      Cc = Cc * Cn;
+    }
+  }
+  T xn = __shfl_down_sync(0xffffffffu, Dc, 1);  // x at the first row of the next lane
+  if (lane == 31) xn = 0;
+#pragma unroll
+  for (int q = KPL - 1; q >= 0; --q) {
+    xn = C[q] * xn + B[q];
+    B[q] = xn;
+  }
+}
+
 // Sweep modes of the smoothers (see k_mg_smooth_mode).
 enum { kSweepPlain = 0, kSweepFromZero = 1, kSweepAfterProlong = 2 };
 
@@ -326,54 +379,67 @@ __global__ void __launch_bounds__(256) k_line_pcr_kernel(int S, LevelView<T> L, 
 
 static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128 ? 4 : 0)); }
 
-// Tiled line smoother: a CTA of 8 warps owns 8 consecutive cells of one
-// colour.  Their K-slice systems are gathered with sector-sized row loads
-// into a padded [K][9] shared tile, warp w solves column w by PCR, and the
-// solutions leave through the same tile.
-constexpr int kTileCells = 8;
-constexpr int kTileThreads = 32 * kTileCells;  // one warp per line of the tile
-
-// The three stages of one tile, run by kTileThreads threads (tid) of a CTA on
-// their own shared tile (3 S (kTileCells+1) values), with a barrier of those
-// threads between stages.  tile: index of the first cell / kTileCells.
-template <typename T, int MODE>
+// Tiled line smoother: a CTA of TC warps owns TC consecutive cells of one
+// colour.  Their K-slice systems are gathered with row loads of TC cells into
+// a padded [K][TC+1] shared tile (each thread loads its KPL rows before using
+// any), warp w solves column w by PCR, and the solutions leave through the
+// same tile.  TC = 8 keeps many CTAs on small levels; TC = 16 gives 64-byte
+// row segments (FP32) on large ones.
+// The three stages of one tile, run by the 32 TC threads (tid) of a CTA on
+// their own shared tile (3 S (TC+1) values), with a barrier of those threads
+// between stages.  tile: index of the first cell / TC.
+template <typename T, int TC, int KPL, int MODE>
 __device__ __forceinline__ void tile_gather(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color,
                                             int tile, int tid, T* tsm) {
-  constexpr int P = kTileCells + 1;
+  constexpr int P = TC + 1;
   T* sd = tsm;           // [S][P] diagonal
   T* sr = sd + S * P;    // [S][P] right-hand side, then solution
   T* st = sr + S * P;    // [S][P] tau
   const int sq = L.m * L.m, ld = (int)L.ld;
-  const int j = tid % kTileCells, row0 = tid / kTileCells;
-  constexpr int rows = kTileThreads / kTileCells;
-  const int cell = tile * kTileCells + j;
+  const int j = tid % TC, row0 = tid / TC;  // rows row0, row0 + 32, ...
+  const int cell = tile * TC + j;
   const bool live = cell < sq;
   i64 nb[3] = {-1, -1, -1};
   const int c = color * sq + cell;
   if (live) neighbours(L.m, decode(L.m, c), nb);
-  for (int k = row0; k < S; k += rows) {
-    T dg = 1, rhs = 0, tau = 0;
-    if (live) {
+  T tau[KPL], bb[KPL], al[KPL][3], xn[KPL][3];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = row0 + 32 * q;
+    tau[q] = 0;
+    bb[q] = 0;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) al[q][sl] = 0, xn[q][sl] = 0;
+    if (live && k < S) {
       const int o = k * ld;
-      tau = L.tau[o + c];
-      dg = 2 * tau;
-      rhs = L.b[o + c];
+      tau[q] = L.tau[o + c];
+      bb[q] = L.b[o + c];
 #pragma unroll
       for (int sl = 0; sl < 3; ++sl) {
-        T al = L.alpha[(sl * S + k) * ld + c];
-        dg += al;
-        if (MODE != kSweepFromZero && nb[sl] >= 0) rhs += al * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
+        al[q][sl] = L.alpha[(sl * S + k) * ld + c];
+        if (MODE != kSweepFromZero && nb[sl] >= 0) xn[q][sl] = sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
       }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = row0 + 32 * q;
+    if (k >= S) continue;
+    T dg = live ? 2 * tau[q] : (T)1, rhs = bb[q];
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      dg += al[q][sl];
+      if (MODE != kSweepFromZero) rhs += al[q][sl] * xn[q][sl];
     }
     sd[k * P + j] = dg;
     sr[k * P + j] = rhs;
-    st[k * P + j] = tau;
+    st[k * P + j] = tau[q];
   }
 }
 
-template <typename T, int KPL>
+template <typename T, int TC, int KPL>
 __device__ __forceinline__ void tile_solve(int S, int tid, T* tsm) {
-  constexpr int P = kTileCells + 1;
+  constexpr int P = TC + 1;
   T* sd = tsm;
   T* sr = sd + S * P;
   T* st = sr + S * P;
@@ -400,28 +466,187 @@ __device__ __forceinline__ void tile_solve(int S, int tid, T* tsm) {
   }
 }
 
-template <typename T>
+template <typename T, int TC, int KPL>
 __device__ __forceinline__ void tile_store(int S, const LevelView<T>& L, int color, int tile, int tid, const T* tsm) {
-  constexpr int P = kTileCells + 1;
+  constexpr int P = TC + 1;
   const T* sr = tsm + S * P;
   const int sq = L.m * L.m, ld = (int)L.ld;
-  const int j = tid % kTileCells, row0 = tid / kTileCells;
-  constexpr int rows = kTileThreads / kTileCells;
-  const int cell = tile * kTileCells + j;
-  if (cell < sq)
-    for (int k = row0; k < S; k += rows) L.x[k * ld + color * sq + cell] = sr[k * P + j];
+  const int j = tid % TC, row0 = tid / TC;
+  const int cell = tile * TC + j;
+  if (cell < sq) {
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int k = row0 + 32 * q;
+      if (k < S) L.x[k * ld + color * sq + cell] = sr[k * P + j];
+    }
+  }
 }
 
-template <typename T, int KPL, int MODE>
-__global__ void __launch_bounds__(kTileThreads) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc,
-                                                                       int color) {
+template <typename T, int TC, int KPL, int MODE>
+__global__ void __launch_bounds__(32 * TC) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tsm = reinterpret_cast<T*>(smem_raw);
-  tile_gather<T, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
+  tile_gather<T, TC, KPL, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
   __syncthreads();
-  tile_solve<T, KPL>(S, threadIdx.x, tsm);
+  tile_solve<T, TC, KPL>(S, threadIdx.x, tsm);
   __syncthreads();
-  tile_store<T>(S, L, color, blockIdx.x, threadIdx.x, tsm);
+  tile_store<T, TC, KPL>(S, L, color, blockIdx.x, threadIdx.x, tsm);
+}
+
+// Thomas factors of every line of a level in device memory (once per Newton step).
+template <typename T>
+__global__ void k_line_factor_kernel(int S, LevelView<T> L) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)L.nc; c += gridDim.x * blockDim.x) line_factor(S, L, c);
+}
+
+template <typename T>
+void k_mg_line_factor(int S, const LevelView<T>& L, Stream st) {
+  if (!L.fac || !L.tau) return;
+  launch(k_line_factor_kernel<T>, nblk(L.nc), kT, 0, cs(st), S, L);
+}
+
+// The tile stages with stored factors: the gather writes the substitution
+// coefficients A = tau/den, B = r/den, C = -cp (tile_gather's right-hand side
+// r), the solve runs scan_tridiag on contiguous rows per lane.
+template <typename T, int TC, int KPL, int MODE>
+__device__ __forceinline__ void tile_gather_fac(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color,
+                                                int tile, int tid, T* tsm) {
+  constexpr int P = TC + 1;
+  T* sa = tsm;
+  T* sb = sa + S * P;
+  T* sc = sb + S * P;
+  const int sq = L.m * L.m, ld = (int)L.ld;
+  const int j = tid % TC, row0 = tid / TC;
+  const int cell = tile * TC + j;
+  const bool live = cell < sq;
+  i64 nb[3] = {-1, -1, -1};
+  const int c = color * sq + cell;
+  if (live) neighbours(L.m, decode(L.m, c), nb);
+  const T* inv = L.fac;
+  const T* cpf = L.fac + (i64)S * ld;
+  T tau[KPL], bb[KPL], iv[KPL], cp[KPL], al[KPL][3], xn[KPL][3];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = row0 + 32 * q;
+    tau[q] = 0, bb[q] = 0, iv[q] = 0, cp[q] = 0;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) al[q][sl] = 0, xn[q][sl] = 0;
+    if (live && k < S) {
+      const int o = k * ld + c;
+      tau[q] = L.tau[o];
+      bb[q] = L.b[o];
+      iv[q] = inv[o];
+      cp[q] = cpf[o];
+      if (MODE != kSweepFromZero) {
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl) {
+          al[q][sl] = L.alpha[(sl * S + k) * ld + c];
+          if (nb[sl] >= 0) xn[q][sl] = sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = row0 + 32 * q;
+    if (k >= S) continue;
+    T rhs = bb[q];
+    if (MODE != kSweepFromZero) {
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) rhs += al[q][sl] * xn[q][sl];
+    }
+    sa[k * P + j] = (k > 0) ? tau[q] * iv[q] : (T)0;
+    sb[k * P + j] = rhs * iv[q];
+    sc[k * P + j] = -cp[q];
+  }
+}
+
+template <typename T, int TC, int KPL>
+__device__ __forceinline__ void tile_solve_fac(int S, int tid, T* tsm) {
+  constexpr int P = TC + 1;
+  T* sa = tsm;
+  T* sb = sa + S * P;
+  T* sc = sb + S * P;
+  const int lane = tid & 31, col = tid >> 5;
+  T A[KPL], B[KPL], C[KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = lane * KPL + q;
+    const bool in = k < S;
+    A[q] = in ? sa[k * P + col] : (T)0;
+    B[q] = in ? sb[k * P + col] : (T)0;
+    C[q] = in ? sc[k * P + col] : (T)0;
+  }
+  __syncwarp();
+  scan_tridiag<T, KPL>(A, B, C, lane);
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int k = lane * KPL + q;
+    if (k < S) sb[k * P + col] = B[q];
+  }
+}
+
+template <typename T, int TC, int KPL, int MODE>
+__global__ void __launch_bounds__(32 * TC) k_line_scan_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tsm = reinterpret_cast<T*>(smem_raw);
+  tile_gather_fac<T, TC, KPL, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
+  __syncthreads();
+  tile_solve_fac<T, TC, KPL>(S, threadIdx.x, tsm);
+  __syncthreads();
+  tile_store<T, TC, KPL>(S, L, color, blockIdx.x, threadIdx.x, tsm);
+}
+
+// Cells per tile of the line smoother for a level of sq cells per colour.
+static inline int tile_cells(i64 sq) { return sq >= 16384 ? 16 : 8; }
+
+template <typename T, int TC, int MODE>
+static void launch_tile_tc(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color, int kpl, Stream st) {
+  const i64 sq = (i64)L.m * L.m;
+  const int blocks = (int)((sq + TC - 1) / TC);
+  const size_t tile = 3 * (size_t)S * (TC + 1) * sizeof(T);
+  if (L.fac) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+    if (kpl == 1)
+      launch(k_line_scan_tile_kernel<T, TC, 1, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
+    else if (kpl == 2)
+      launch(k_line_scan_tile_kernel<T, TC, 2, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
+    else
+      launch(k_line_scan_tile_kernel<T, TC, 4, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
+    return;
+  }
+  if (kpl == 1)
+    launch(k_line_pcr_tile_kernel<T, TC, 1, MODE>, blocks, 32 * TC, tile, reinterpret_cast<cudaStream_t>(st), S, L, Lc,
+           color);
+  else if (kpl == 2)
+    launch(k_line_pcr_tile_kernel<T, TC, 2, MODE>, blocks, 32 * TC, tile, reinterpret_cast<cudaStream_t>(st), S, L, Lc,
+           color);
+  else
+    launch(k_line_pcr_tile_kernel<T, TC, 4, MODE>, blocks, 32 * TC, tile, reinterpret_cast<cudaStream_t>(st), S, L, Lc,
+           color);
+}
+
+// The tile width for this shape, or 0 if no tiled sweep applies (K > 128, a tile
+// beyond 48 KB of shared memory, or indices beyond 32 bits).
+template <typename T>
+static int tile_width(int S, const LevelView<T>& L) {
+  int tc = tile_cells((i64)L.m * L.m);
+  if (3 * (size_t)S * (tc + 1) * sizeof(T) > 48 * 1024) tc = 8;
+  if (pcr_kpl(S) == 0 || 3 * (size_t)S * (tc + 1) * sizeof(T) > 48 * 1024 || 3 * (i64)S * L.ld >= (1ll << 31)) return 0;
+  return tc;
+}
+
+// The tiled line sweep of one colour in a mode, if the shape allows one; false otherwise.
+template <typename T, int MODE>
+static bool launch_tile(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color, Stream st) {
+  const int kpl = pcr_kpl(S);
+  const int tc = tile_width(S, L);
+  if (tc == 0) return false;
+  if (tc == 16)
+    launch_tile_tc<T, 16, MODE>(S, L, Lc, color, kpl, st);
+  else
+    launch_tile_tc<T, 8, MODE>(S, L, Lc, color, kpl, st);
+  return true;
 }
 
 // Opt a kernel into more than 48 KB of dynamic shared memory (once per size).
@@ -445,15 +670,7 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
   prof::begin(id, st);
   if (L.tau) {
     int kpl = pcr_kpl(S);
-    const size_t tile = 3 * (size_t)S * (kTileCells + 1) * sizeof(T);
-    if (kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.ld < (1ll << 31)) {
-      int blocks = (int)((sq + kTileCells - 1) / kTileCells);
-      if (kpl == 1)
-        launch(k_line_pcr_tile_kernel<T, 1, kSweepPlain>, blocks, 32 * kTileCells, tile, cs(st), S, L, L, color);
-      else if (kpl == 2)
-        launch(k_line_pcr_tile_kernel<T, 2, kSweepPlain>, blocks, 32 * kTileCells, tile, cs(st), S, L, L, color);
-      else
-        launch(k_line_pcr_tile_kernel<T, 4, kSweepPlain>, blocks, 32 * kTileCells, tile, cs(st), S, L, L, color);
+    if (launch_tile<T, kSweepPlain>(S, L, L, color, st)) {
       prof::end(id, st, (double)sizeof(T) * 7.0 * (double)S * (double)sq);
       return;
     }
@@ -493,9 +710,7 @@ void k_mg_smooth_mode(int S, const LevelView<T>& L, const LevelView<T>* coarse, 
   const LevelView<T> Lc = coarse ? *coarse : L;
   const i64 sq = (i64)L.m * L.m;
   const int id = L.tau ? prof::SCH_SMOOTH : prof::LAP_SMOOTH;
-  const int kpl = L.tau ? pcr_kpl(S) : 0;
-  const size_t tile = 3 * (size_t)S * (kTileCells + 1) * sizeof(T);
-  if (L.tau && !(kpl > 0 && tile <= 48 * 1024 && 3 * (i64)S * L.ld < (1ll << 31))) {
+  if (L.tau && tile_width(S, L) == 0) {
     // no tiled kernel for this shape: make the mode explicit, then a plain sweep
     if (mode == kSweepFromZero)
       dev::zero(L.x, sizeof(T) * (size_t)S * L.ld, st);
@@ -506,25 +721,10 @@ void k_mg_smooth_mode(int S, const LevelView<T>& L, const LevelView<T>* coarse, 
   }
   prof::begin(id, st);
   if (L.tau) {
-    const int blocks = (int)((sq + kTileCells - 1) / kTileCells);
-    const int thr = 32 * kTileCells;
-#define OT_TILE(Q, M) launch(k_line_pcr_tile_kernel<T, Q, M>, blocks, thr, tile, cs(st), S, L, Lc, color)
-    if (mode == kSweepFromZero) {
-      if (kpl == 1)
-        OT_TILE(1, kSweepFromZero);
-      else if (kpl == 2)
-        OT_TILE(2, kSweepFromZero);
-      else
-        OT_TILE(4, kSweepFromZero);
-    } else {
-      if (kpl == 1)
-        OT_TILE(1, kSweepAfterProlong);
-      else if (kpl == 2)
-        OT_TILE(2, kSweepAfterProlong);
-      else
-        OT_TILE(4, kSweepAfterProlong);
-    }
-#undef OT_TILE
+    if (mode == kSweepFromZero)
+      launch_tile<T, kSweepFromZero>(S, L, Lc, color, st);
+    else
+      launch_tile<T, kSweepAfterProlong>(S, L, Lc, color, st);
   } else if (mode == kSweepFromZero) {
     if (point_rows_ok(S, L))
       launch_point_rows<T, kSweepFromZero>(S, L, Lc, color, st);
@@ -586,10 +786,57 @@ __global__ void k_restrict_residual_kernel(int S, LevelView<T> f, LevelView<T> c
   }
 }
 
+// level_apply for fine triangle (t, I, J) in the row layout (32-bit indices).
+template <typename T>
+__device__ __forceinline__ T level_apply_row(int S, const LevelView<T>& L, int k, int t, int I, int J) {
+  const int m = L.m, ld = (int)L.ld;
+  const int c = t * m * m + J * m + I;
+  const T* xs = L.x + k * ld;
+  const T xc = xs[c];
+  T acc = 0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    int Io, Jo;
+    const int o = row_nb(m, t, I, J, sl, &Io, &Jo);
+    if (o < 0) continue;
+    acc += L.alpha[(sl * S + k) * ld + c] * (xc - xs[o]);
+  }
+  if (L.tau) {
+    const T xm = (k > 0) ? L.x[(k - 1) * ld + c] : (T)0;
+    const T xp = (k < S - 1) ? L.x[(k + 1) * ld + c] : (T)0;
+    acc += L.tau[k * ld + c] * (2 * xc - xm - xp);
+  }
+  return acc;
+}
+
+// b_coarse = J^T (b - M x) with a warp per row of coarse squares (as k_restrict_residual_kernel).
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_residual_rows(int S, LevelView<T> f, LevelView<T> c) {
+  const int n = c.m, nn = n * n, m = f.m, mm = m * m, fld = (int)f.ld, cld = (int)c.ld;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  for (int k = blockIdx.z; k < S; k += gridDim.z) {
+    const T* bf = f.b + k * fld;
+    for (int t = 0; t < 2; ++t) {
+      int ct[4], cI[4], cJ[4];
+      row_children(t, i, j, ct, cI, cJ);
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += bf[ct[a] * mm + cJ[a] * m + cI[a]] - level_apply_row(S, f, k, ct[a], cI[a], cJ[a]);
+      c.b[k * cld + t * nn + j * n + i] = acc;
+    }
+  }
+}
+
 template <typename T>
 void k_mg_restrict_residual(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st) {
   prof::begin(prof::MG_TRANSFER, st);
-  launch(k_restrict_residual_kernel<T>, slice_grid(coarse.nc, S), kT, 0, cs(st), S, fine, coarse);
+  if (point_rows_ok(S, fine) && point_rows_ok(S, coarse)) {
+    const dim3 grid((unsigned)((coarse.m + 31) / 32), (unsigned)((coarse.m + 7) / 8), (unsigned)(S < 65535 ? S : 65535));
+    launch(k_restrict_residual_rows<T>, grid, dim3(32, 8), 0, cs(st), S, fine, coarse);
+  } else {
+    launch(k_restrict_residual_kernel<T>, slice_grid(coarse.nc, S), kT, 0, cs(st), S, fine, coarse);
+  }
   prof::end(prof::MG_TRANSFER, st, (double)sizeof(T) * (fine.tau ? 6.0 : 5.0) * (double)S * (double)fine.nc);
 }
 
@@ -650,13 +897,9 @@ __device__ __forceinline__ void line_factor(int S, const LevelView<T>& L, int c)
   }
 }
 
-// One colour sweep of a staged level with the stored factors, one warp per
-// line, lane l holding rows l KPL .. l KPL + KPL - 1.  The lanes form their
-// rows' right-hand sides b + sum_slot alpha x_neighbour (neighbour values as
-// the sweep mode gives them) in parallel; the substitutions are linear
-// recurrences, rp_k = (tau_k/den_k) rp_{k-1} + r_k/den_k forward and
-// x_k = -cp_k x_{k+1} + rp_k back, each solved by composing the affine maps
-// within a lane and then across the warp by a shuffle scan (log2 32 steps).
+// One line of a staged level by one warp with the stored factors: the lanes
+// form their rows' right-hand sides b + sum_slot alpha x_neighbour (neighbour
+// values as the sweep mode gives them) in parallel, then scan_tridiag.
 template <typename T, int KPL, int MODE>
 __device__ __forceinline__ void line_scan_solve(int S, const LevelView<T>& L, const LevelView<T>& Lc, int c,
                                                 int lane) {
@@ -686,50 +929,11 @@ __device__ __forceinline__ void line_scan_solve(int S, const LevelView<T>& L, co
       C[q] = -cp[o];
     }
   }
-  // forward: the lane's composed map, an inclusive scan over lanes, then the rows
-  T Aa = A[0], Ba = B[0];
-#pragma unroll
-  for (int q = 1; q < KPL; ++q) {
-    Ba = A[q] * Ba + B[q];
-    Aa = A[q] * Aa;
-  }
-#pragma unroll
-  for (int s = 1; s < 32; s <<= 1) {
-    const T Ap = __shfl_up_sync(0xffffffffu, Aa, s), Bp = __shfl_up_sync(0xffffffffu, Ba, s);
-    if (lane >= s) {
-      Ba = Aa * Bp + Ba;
-      Aa = Aa * Ap;
-    }
-  }
-  T rp = __shfl_up_sync(0xffffffffu, Ba, 1);  // rp at the last row of the previous lane
-  if (lane == 0) rp = 0;
+  scan_tridiag<T, KPL>(A, B, C, lane);
 #pragma unroll
   for (int q = 0; q < KPL; ++q) {
-    rp = A[q] * rp + B[q];
-    B[q] = rp;  // B now holds rp
-  }
-  // back: x_k = C_k x_{k+1} + rp_k, composed from the end
-  T Cc = C[KPL - 1], Dc = B[KPL - 1];
-#pragma unroll
-  for (int q = KPL - 2; q >= 0; --q) {
-    Dc = C[q] * Dc + B[q];
-    Cc = C[q] * Cc;
-  }
-#pragma unroll
-  for (int s = 1; s < 32; s <<= 1) {
-    const T Cn = __shfl_down_sync(0xffffffffu, Cc, s), Dn = __shfl_down_sync(0xffffffffu, Dc, s);
-    if (lane + s < 32) {
-      Dc = Cc * Dn + Dc;
-      Cc = Cc * Cn;
-    }
-  }
-  T xn = __shfl_down_sync(0xffffffffu, Dc, 1);  // x at the first row of the next lane
-  if (lane == 31) xn = 0;
-#pragma unroll
-  for (int q = KPL - 1; q >= 0; --q) {
-    xn = C[q] * xn + B[q];
     const int k = lane * KPL + q;
-    if (k < S) L.x[(i64)k * ld + c] = xn;
+    if (k < S) L.x[(i64)k * ld + c] = B[q];
   }
 }
 
@@ -1195,6 +1399,7 @@ void k_mg_store(const T* x, double* dst, i64 n, Stream st) {
   template void k_mg_coarse_solve<T>(int, const LevelView<T>&, int, T*, T*, T*, Stream);                       \
   template void k_mg_lower_cycle<T>(int, const LevelView<T>*, int, int, int, T*, T*, T*, Stream);              \
   template void k_mg_prepare_lower_cycle<T>(int, const LevelView<T>*, int);                                    \
+  template void k_mg_line_factor<T>(int, const LevelView<T>&, Stream);                                         \
   template size_t k_mg_fused_smem<T>(int, const LevelView<T>*, int);                                           \
   template void k_mg_load<T>(const double*, double, T*, T*, i64, Stream);                                      \
   template void k_mg_store<T>(const T*, double*, i64, Stream);

@@ -28,6 +28,208 @@ __device__ __forceinline__ double warp_sum2(double v) {
   return v;
 }
 
+// ------------------------------------------------------------------ row-layout stencils
+// A warp takes one row J of squares, its lanes the squares I (blockIdx.z walks
+// the slices); each thread handles both triangles of its square.  Neighbours,
+// parents and children by the row helpers of stencil.cuh; the operations are
+// those of the per-cell bodies, in the same order.
+static inline dim3 rows_grid(int side, int S) {
+  return dim3((unsigned)((side + 31) / 32), (unsigned)((side + 7) / 8), (unsigned)(S < 65535 ? (S > 0 ? S : 1) : 65535));
+}
+static const dim3 kRowsBlock(32, 8);
+#define ROWS_SQUARE(side, I, J)                    \
+  const int I = blockIdx.x * 32 + threadIdx.x;     \
+  const int J = blockIdx.y * 8 + threadIdx.y;      \
+  if (I >= (side) || J >= (side)) return;
+
+// u = M^{-1} B~ z (schur_u) on the fine grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_schur_u_rows(Dims d, const T* __restrict__ phi, const T* __restrict__ z,
+                                                      T* __restrict__ u) {
+  const int m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
+  ROWS_SQUARE(m, I, J)
+  for (int jj = blockIdx.z; jj < d.K + 1; jj += gridDim.z) {
+    const T* ph = phi + (i64)jj * N;
+    const T* zm = (jj >= 1) ? z + (i64)(jj - 1) * Nc : nullptr;
+    const T* zp = (jj <= d.K - 1) ? z + (i64)jj * Nc : nullptr;
+    for (int t = 0; t < 2; ++t) {
+      const int c = t * mm + J * m + I;
+      const int P = row_parent(m, t, I, J);
+      const T zmc = zm ? zm[P] : (T)0, zpc = zp ? zp[P] : (T)0;
+      const T zbc = (T)0.5 * (zmc + zpc);
+      const T pc = ph[c];
+      T acc = (T)0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        int Io, Jo;
+        const int o = row_nb(m, t, I, J, sl, &Io, &Jo);
+        if (o < 0) continue;
+        const int Po = row_parent(m, 1 - t, Io, Jo);
+        const T zbo = (T)0.5 * ((zm ? zm[Po] : (T)0) + (zp ? zp[Po] : (T)0));
+        acc += (T)trans(sl) * (pc - ph[o]) * (zbc - zbo);
+      }
+      u[(i64)jj * N + c] = (zpc - zmc) / (T)d.dt + (T)0.5 * acc / (T)d.area_f;
+    }
+  }
+}
+
+// out = s (A~ z) - rho (B u) (schur_out) on the coarse grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_schur_out_rows(Dims d, const T* __restrict__ phi, const T* __restrict__ rho,
+                                                        const T* __restrict__ s, const T* __restrict__ u,
+                                                        const T* __restrict__ z, T* __restrict__ out) {
+  const int n = d.n, nn = n * n, m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
+  ROWS_SQUARE(n, i, j)
+  for (int k0 = blockIdx.z; k0 < d.K; k0 += gridDim.z) {
+    const T* rk = rho + (i64)k0 * Nc;
+    const T* zk = z + (i64)k0 * Nc;
+    const T* p0 = phi + (i64)k0 * N;
+    const T* p1 = p0 + N;
+    const T* x0 = u + (i64)k0 * N;
+    const T* x1 = x0 + N;
+    for (int t = 0; t < 2; ++t) {
+      const int C = t * nn + j * n + i;
+      // A~ z (apply_atilde)
+      T at = (T)0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        int io, jo;
+        const int O = row_nb(n, t, i, j, sl, &io, &jo);
+        if (O < 0) continue;
+        at += (T)trans(sl) * (T)0.5 * (rk[C] + rk[O]) * (zk[C] - zk[O]);
+      }
+      // B u (apply_B)
+      int ct[4], cI[4], cJ[4];
+      row_children(t, i, j, ct, cI, cJ);
+      T acc = (T)0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int c = ct[a] * mm + cJ[a] * m + cI[a];
+        acc += (T)d.area_f * (x1[c] - x0[c]) / (T)d.dt;
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl) {
+          int Io, Jo;
+          const int o = row_nb(m, ct[a], cI[a], cJ[a], sl, &Io, &Jo);
+          if (o < 0) continue;
+          acc += (T)0.25 * (T)trans(sl) * ((p0[c] - p0[o]) * (x0[c] - x0[o]) + (p1[c] - p1[o]) * (x1[c] - x1[o]));
+        }
+      }
+      const i64 idx = (i64)k0 * Nc + C;
+      out[idx] = s[idx] * at - rho[idx] * acc;
+    }
+  }
+}
+
+// phi rows of [A, B^T P^T] x from the edge coefficients (kkt_phi_sliced).
+// With e non-null (and with_a) it also writes e^jj_c = sum_slot g_slot (x_c - x_o), the
+// B part of the rho rows at this cell, from the coefficients and values it has loaded.
+__global__ void __launch_bounds__(256) k_kkt_phi_sliced_rows(Dims d, const double* __restrict__ kc,
+                                                             const double* __restrict__ xp,
+                                                             const double* __restrict__ yb, bool with_a,
+                                                             double* __restrict__ y, double* __restrict__ e) {
+  const int m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
+  ROWS_SQUARE(m, I, J)
+  for (int jj = blockIdx.z; jj < d.K + 1; jj += gridDim.z) {
+    const double* ybar = yb + (i64)jj * Nc;
+    const double* ydif = yb + (i64)(d.K + 1 + jj) * Nc;
+    const double* xs = with_a ? xp + (i64)jj * N : nullptr;
+    for (int t = 0; t < 2; ++t) {
+      const int c = t * mm + J * m + I;
+      const int P = row_parent(m, t, I, J);
+      double acc = ydif[P];
+      const double ybc = ybar[P];
+      const double xc = with_a ? xs[c] : 0.0;
+      const double* kw = kc + (i64)jj * 6 * N + c;
+      double ec = 0.0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        int Io, Jo;
+        const int o = row_nb(m, t, I, J, sl, &Io, &Jo);
+        if (o < 0) continue;
+        const double g = kw[(i64)(3 + sl) * N];
+        acc += g * (ybc + ybar[row_parent(m, 1 - t, Io, Jo)]);
+        if (with_a) {
+          const double dx = xc - xs[o];
+          acc += kw[(i64)sl * N] * dx;
+          ec += g * dx;
+        }
+      }
+      y[(i64)jj * N + c] = acc;
+      if (e) e[(i64)jj * N + c] = ec;
+    }
+  }
+}
+
+// rho rows before the projection: (B x_phi)^k - |C| s/rho (x_rho - mean), the B part
+// (apply_B_cached) summed over the four children from the edge sums e of the phi rows:
+//   (B x)^k_C = sum_{c in C} [ |c| (x^{k+1}_c - x^k_c)/dt + (e^k_c + e^{k+1}_c)/2 ].
+__global__ void __launch_bounds__(256) k_kkt_rho_rows(Dims d, const double* __restrict__ kc,
+                                                      const double* __restrict__ xp, const double* __restrict__ e,
+                                                      const double* __restrict__ xr,
+                                                      const double* __restrict__ xmean, double* __restrict__ w) {
+  const int n = d.n, nn = n * n, m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
+  const double* sr = kc + (i64)(d.K + 1) * 6 * d.N;
+  ROWS_SQUARE(n, i, j)
+  for (int k0 = blockIdx.z; k0 < d.K; k0 += gridDim.z) {
+    const double* x0 = xp + (i64)k0 * N;
+    const double* x1 = x0 + N;
+    const double* e0 = e + (i64)k0 * N;
+    const double* e1 = e0 + N;
+    for (int t = 0; t < 2; ++t) {
+      const int C = t * nn + j * n + i;
+      int ct[4], cI[4], cJ[4];
+      row_children(t, i, j, ct, cI, cJ);
+      double dtime = 0.0, edges = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int c = ct[a] * mm + cJ[a] * m + cI[a];
+        dtime += x1[c] - x0[c];
+        edges += e0[c] + e1[c];
+      }
+      const i64 idx = (i64)k0 * Nc + C;
+      w[idx] = d.af_dt * dtime + 0.5 * edges - sr[idx] * (xr[idx] - xmean[k0]);
+    }
+  }
+}
+
+// phi rows of [A, B^T P^T] x computed from phi (kkt_phi), for the FP32 B^T P^T of the preconditioner.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kkt_phi_rows(Dims d, const T* __restrict__ phi, const T* __restrict__ rho,
+                                                      const T* __restrict__ r0, const T* __restrict__ r1,
+                                                      const T* __restrict__ xp, const T* __restrict__ xr,
+                                                      const T* __restrict__ xmean, bool with_a, T* __restrict__ y) {
+  const int m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
+  ROWS_SQUARE(m, I, J)
+  for (int jj = blockIdx.z; jj < d.K + 1; jj += gridDim.z) {
+    const T* ph = phi + (i64)jj * N;
+    const T* xs = with_a ? xp + (i64)jj * N : nullptr;
+    const T* ym = (jj >= 1) ? xr + (i64)(jj - 1) * Nc : nullptr;
+    const T* yp = (jj <= d.K - 1) ? xr + (i64)jj * Nc : nullptr;
+    const T mmn = (jj >= 1) ? xmean[jj - 1] : (T)0, mpn = (jj <= d.K - 1) ? xmean[jj] : (T)0;
+    for (int t = 0; t < 2; ++t) {
+      const int c = t * mm + J * m + I;
+      const int P = row_parent(m, t, I, J);
+      const T yma = ym ? ym[P] - mmn : (T)0, ypa = yp ? yp[P] - mpn : (T)0;
+      T acc = (T)d.area_f * (yma - ypa) / (T)d.dt;
+      const T ybc = (T)0.5 * (yma + ypa);
+      const T rc = with_a ? rho_bar(d, rho, r0, r1, jj, (i64)P) : (T)0;
+      const T pc = ph[c], xc = with_a ? xs[c] : (T)0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        int Io, Jo;
+        const int o = row_nb(m, t, I, J, sl, &Io, &Jo);
+        if (o < 0) continue;
+        const int Po = row_parent(m, 1 - t, Io, Jo);
+        const T ybo = (T)0.5 * ((ym ? ym[Po] - mmn : (T)0) + (yp ? yp[Po] - mpn : (T)0));
+        T term = (T)0.5 * (ybc + ybo) * (pc - ph[o]);
+        if (with_a) term += (T)0.5 * (rc + rho_bar(d, rho, r0, r1, jj, (i64)Po)) * (xc - xs[o]);
+        acc += (T)trans(sl) * term;
+      }
+      y[(i64)jj * N + c] = acc;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ residual
 __global__ void k_residual_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0,
                                       const double* r1, double* F) {
@@ -128,19 +330,7 @@ __global__ void k_kkt_slice_values_kernel(Dims d, const double* xr, const double
   SLICE_LOOP(jj, d.K + 1, C, d.Nc) kkt_slice_values(d, xr, xmean, jj, C, yb);
 }
 
-__global__ void k_kkt_phi_sliced_kernel(Dims d, const double* kc, const double* xp, const double* yb, bool with_a,
-                                        double* y) {
-  SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi_sliced(d, kc, xp, yb, with_a, jj, c);
-}
 
-__global__ void k_kkt_rho_cached_kernel(Dims d, const double* kc, const double* xp, const double* xr,
-                                        const double* xmean, double* w) {
-  const double* sr = kc + (i64)(d.K + 1) * 6 * d.N;
-  SLICE_LOOP(k0, d.K, C, d.Nc) {
-    const i64 idx = (i64)k0 * d.Nc + C;
-    w[idx] = apply_B_cached(d, kc, xp, k0, C) - sr[idx] * (xr[idx] - xmean[k0]);
-  }
-}
 
 void k_kkt_apply(const Dims& d, const double* kc, const double* x, double* y, double* xmean, double* wsum,
                  Stream st) {
@@ -150,8 +340,11 @@ void k_kkt_apply(const Dims& d, const double* kc, const double* x, double* y, do
   double* yb = const_cast<double*>(kc) + kkt_yb_offset(d);
   launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), xr, d.Nc, xmean);
   launch(k_kkt_slice_values_kernel, slice_grid(d.Nc, d.K + 1), kT, 0, cs(st), d, xr, (const double*)xmean, yb);
-  launch(k_kkt_phi_sliced_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, x, (const double*)yb, true, y);
-  launch(k_kkt_rho_cached_kernel, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, kc, x, xr, (const double*)xmean, y + Np);
+  double* e = const_cast<double*>(kc) + kkt_e_offset(d);
+  launch(k_kkt_phi_sliced_rows, rows_grid(d.m, d.K + 1), kRowsBlock, 0, cs(st), d, kc, x, (const double*)yb, true, y,
+         e);
+  launch(k_kkt_rho_rows, rows_grid(d.n, d.K), kRowsBlock, 0, cs(st), d, kc, x, (const double*)e, xr,
+         (const double*)xmean, y + Np);
   launch(k_project_kernel, d.K, 1024, 0, cs(st), y + Np, d.Nc, wsum);
   // x, y on both blocks, the six edge coefficients per fine cell and |C| s/rho
   prof::end(prof::KKT, st, 8.0 * (2.0 * Np + 2.0 * d.K * d.Nc + 6.0 * Np + d.K * d.Nc));
@@ -200,27 +393,20 @@ void k_bt_apply(const Dims& d, const double* kc, const double* yr, double* out_p
   launch(k_slice_mean_kernel<double>, d.K, 1024, 0, cs(st), yr, d.Nc, yr_mean);
   double* yb = const_cast<double*>(kc) + kkt_yb_offset(d);
   launch(k_kkt_slice_values_kernel, slice_grid(d.Nc, d.K + 1), kT, 0, cs(st), d, yr, (const double*)yr_mean, yb);
-  launch(k_kkt_phi_sliced_kernel, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, kc, (const double*)nullptr,
-         (const double*)yb, false, out_phi);
+  launch(k_kkt_phi_sliced_rows, rows_grid(d.m, d.K + 1), kRowsBlock, 0, cs(st), d, kc, (const double*)nullptr,
+         (const double*)yb, false, out_phi, (double*)nullptr);
   prof::end(prof::BT, st, 8.0 * (2.0 * Np + (double)d.K * d.Nc + 3.0 * Np));
 }
 
 // ------------------------------------------------------------------ Schur operator
-template <typename T>
-__global__ void k_schur_u_kernel(Dims d, const T* phi, const T* z, T* u) {
-  SLICE_LOOP(jj, d.K + 1, c, d.N) u[(i64)jj * d.N + c] = schur_u(d, phi, z, jj, c);
-}
 
-template <typename T>
-__global__ void k_schur_out_kernel(Dims d, const T* phi, const T* rho, const T* s, const T* u, const T* z, T* out) {
-  SLICE_LOOP(k0, d.K, C, d.Nc) out[(i64)k0 * d.Nc + C] = schur_out(d, phi, rho, s, u, z, k0, C);
-}
 
 void k_schur_apply(const Dims& d, const double* phi, const double* rho, const double* s, const double* z,
                    double* out, double* u, Stream st) {
   prof::begin(prof::SCHUR, st);
-  launch(k_schur_u_kernel<double>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, z, u);
-  launch(k_schur_out_kernel<double>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, u, z, out);
+  launch(k_schur_u_rows<double>, rows_grid(d.m, d.K + 1), kRowsBlock, 0, cs(st), d, phi, z, u);
+  launch(k_schur_out_rows<double>, rows_grid(d.n, d.K), kRowsBlock, 0, cs(st), d, phi, rho, s, (const double*)u, z,
+         out);
   prof::end(prof::SCHUR, st, 8.0 * ((double)(d.K + 1) * d.N + 4.0 * d.K * d.Nc));
 }
 
@@ -466,7 +652,7 @@ void k_bt_apply(const Dims& d, const float* phi, const float* yr, float* out_phi
   i64 Np = (i64)(d.K + 1) * d.N;
   prof::begin(prof::BT, st);
   launch(k_slice_mean_kernel<float>, d.K, 1024, 0, cs(st), yr, d.Nc, yr_mean);
-  launch(k_kkt_phi_kernel<float>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, (const float*)nullptr,
+  launch(k_kkt_phi_rows<float>, rows_grid(d.m, d.K + 1), kRowsBlock, 0, cs(st), d, phi, (const float*)nullptr,
          (const float*)nullptr, (const float*)nullptr, (const float*)nullptr, yr, (const float*)yr_mean, false, out_phi);
   prof::end(prof::BT, st, 4.0 * (2.0 * Np + (double)d.K * d.Nc));
 }
@@ -474,8 +660,8 @@ void k_bt_apply(const Dims& d, const float* phi, const float* yr, float* out_phi
 void k_schur_apply(const Dims& d, const float* phi, const float* rho, const float* s, const float* z, float* out,
                    float* u, Stream st) {
   prof::begin(prof::SCHUR, st);
-  launch(k_schur_u_kernel<float>, slice_grid(d.N, d.K + 1), kT, 0, cs(st), d, phi, z, u);
-  launch(k_schur_out_kernel<float>, slice_grid(d.Nc, d.K), kT, 0, cs(st), d, phi, rho, s, (const float*)u, z, out);
+  launch(k_schur_u_rows<float>, rows_grid(d.m, d.K + 1), kRowsBlock, 0, cs(st), d, phi, z, u);
+  launch(k_schur_out_rows<float>, rows_grid(d.n, d.K), kRowsBlock, 0, cs(st), d, phi, rho, s, (const float*)u, z, out);
   prof::end(prof::SCHUR, st, 4.0 * ((double)(d.K + 1) * d.N + 4.0 * d.K * d.Nc));
 }
 

@@ -323,9 +323,10 @@ struct LevelView {
   T* b;
   T* r;
   // Thomas factors of the time lines, [2][S][ld] (1/pivot, then the modified
-  // upper coefficient), on the shared-memory copies of the fused space-time
-  // levels only (nullptr elsewhere): the line systems change once per Newton
-  // step, so a fused cycle factors them once and every sweep only substitutes.
+  // upper coefficient), on the space-time levels swept by tiles (device memory,
+  // refreshed with the coefficients) and on the shared-memory copies of the
+  // fused levels (factored at the start of each fused cycle); nullptr elsewhere.
+  // The line systems change once per Newton step; every sweep only substitutes.
   T* fac = nullptr;
 };
 
@@ -336,6 +337,10 @@ void k_mg_schur_coef0(const Dims& d, const double* phi, const double* rho, const
                       Stream st);
 template <typename T>
 void k_mg_restrict_coef(int S, const LevelView<T>& fine, const LevelView<T>& coarse, Stream st);
+// Thomas factors of every time line of a space-time level (L.fac in device
+// memory; nothing if the level has none): once per Newton step, after the coefficients.
+template <typename T>
+void k_mg_line_factor(int S, const LevelView<T>& L, Stream st);
 template <typename T>
 void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, Stream st);
 // A sweep of one colour in a mode: 0 plain; 1 the first sweep from x = 0

@@ -32,6 +32,7 @@ void Hierarchy<T>::build(int m0, int S_, bool tc) {
     L.x = (T*)dev::alloc(v);
     L.b = (T*)dev::alloc(v);
     L.r = (T*)dev::alloc(v);
+    L.fac = tc ? (T*)dev::alloc(2 * v) : nullptr;
     lv.push_back(L);
     if (m % 2 != 0 || m == 1) break;
     m /= 2;
@@ -67,6 +68,7 @@ void Hierarchy<T>::release() {
     dev::release(L.x);
     dev::release(L.b);
     dev::release(L.r);
+    dev::release(L.fac);
   }
   lv.clear();
   dev::release(line_c);
@@ -329,6 +331,8 @@ static void refresh_t(Workspace& W, Hierarchy<T>& lap, Hierarchy<T>& sch, Stream
   for (size_t l = 0; l + 1 < lap.lv.size(); ++l) k_mg_restrict_coef<T>(lap.S, lap.lv[l], lap.lv[l + 1], st);
   k_mg_schur_coef0<T>(W.d, W.phi, W.rho, W.s, sch.lv[0].alpha, sch.lv[0].tau, st);
   for (size_t l = 0; l + 1 < sch.lv.size(); ++l) k_mg_restrict_coef<T>(sch.S, sch.lv[l], sch.lv[l + 1], st);
+  // time-line factors of the levels the tiled smoother sweeps (the fused levels factor their own)
+  for (size_t l = 0; l < sch.lv.size() && l < sch.fuse_from; ++l) k_mg_line_factor<T>(sch.S, sch.lv[l], st);
 }
 
 void refresh_coefficients(Workspace& W, Stream st) {

@@ -289,7 +289,11 @@ OT_HD T kkt_rho(const Dims& d, const T* phi, const T* rho, const T* s, const T* 
 // 2(K+1)N' values after those are scratch of each application (the slice
 // values of kkt_slice_values).
 OT_HD i64 kkt_yb_offset(const Dims& d) { return (i64)(d.K + 1) * 6 * d.N + (i64)d.K * d.Nc; }
-OT_HD i64 kkt_coef_count(const Dims& d) { return kkt_yb_offset(d) + 2LL * (d.K + 1) * d.Nc; }
+// After the slice values: per potential slice and fine cell, the edge sum
+// e^jj_c = sum_slot g_slot (x^jj_c - x^jj_o) of the B part, written by the phi
+// rows of an application and summed over the four children by its rho rows.
+OT_HD i64 kkt_e_offset(const Dims& d) { return kkt_yb_offset(d) + 2LL * (d.K + 1) * d.Nc; }
+OT_HD i64 kkt_coef_count(const Dims& d) { return kkt_e_offset(d) + (i64)(d.K + 1) * d.N; }
 
 OT_HD void kkt_edge_coef(const Dims& d, const double* phi, const double* rho, const double* r0, const double* r1,
                          int jj, i64 c, double w[3], double g[3]) {
@@ -620,6 +624,48 @@ OT_HD double schur_coef(const Dims& d, const double* phi, const double* rho, con
 
 OT_HD double schur_tau(const Dims& d, const double* rho, int k0, i64 C) {
   return rho[(i64)k0 * d.Nc + C] * d.area_c / (d.dt * d.dt);
+}
+
+// ----------------------------------------------------------------- row layout
+// The same geometry for kernels that give a warp one row J of squares and its
+// lanes the squares I: a triangle is (t, I, J) and its neighbours and parents
+// follow by additions in 32-bit arithmetic, with no index division.  Slot order
+// and boundary rule as in neighbours(); parent and children as parent() and
+// children().
+
+// Neighbour of slot sl of triangle (t, I, J) on a grid of side m: its index,
+// or -1 on the boundary; (I, J) of the neighbour in *Io, *Jo (type 1 - t).
+OT_HD int row_nb(int m, int t, int I, int J, int sl, int* Io, int* Jo) {
+  int a = I, b = J;
+  if (sl == 1) a += (t == 0) ? 1 : -1;
+  if (sl == 2) b += (t == 0) ? -1 : 1;
+  *Io = a;
+  *Jo = b;
+  if (a < 0 || a >= m || b < 0 || b >= m) return -1;
+  return (1 - t) * m * m + b * m + a;
+}
+
+// Coarse triangle (grid side m/2) containing fine triangle (t, I, J) of side m.
+OT_HD int row_parent(int m, int t, int I, int J) {
+  const int n = m >> 1, a = I & 1, b = J & 1;
+  const int tc = (t == 0) ? ((a == 0 && b == 1) ? 1 : 0) : ((a == 1 && b == 0) ? 0 : 1);
+  return tc * n * n + (J >> 1) * n + (I >> 1);
+}
+
+// The four fine triangles (side 2n) of coarse triangle (t, i, j) of side n, as (type, I, J).
+OT_HD void row_children(int t, int i, int j, int ct[4], int cI[4], int cJ[4]) {
+  const int I = 2 * i, J = 2 * j;
+  if (t == 0) {
+    ct[0] = 0, cI[0] = I, cJ[0] = J;
+    ct[1] = 0, cI[1] = I + 1, cJ[1] = J + 1;
+    ct[2] = 0, cI[2] = I + 1, cJ[2] = J;
+    ct[3] = 1, cI[3] = I + 1, cJ[3] = J;
+  } else {
+    ct[0] = 1, cI[0] = I, cJ[0] = J;
+    ct[1] = 1, cI[1] = I + 1, cJ[1] = J + 1;
+    ct[2] = 0, cI[2] = I, cJ[2] = J + 1;
+    ct[3] = 1, cI[3] = I, cJ[3] = J + 1;
+  }
 }
 
 }  // namespace ot
