@@ -148,8 +148,8 @@ def summarise_clocks(lines) -> dict | None:
 # at two smaller sizes, times its first Newton steps there, and the per-step time is carried to the
 # workload's unknown count with the growth exponent those two sizes show, times the Newton steps of
 # the solve: an extrapolation, labelled as such.
-ORACLE_SAMPLES = [(16, 2), (24, 2)]   # (squares per side n, Newton steps timed); K = n/2 as in the workload
-REFERENCE_SAMPLES = [(16, 1), (24, 1)]  # one Newton step per size for each step of the reference arm
+ORACLE_SAMPLES = [(12, 2), (18, 2), (24, 2)]   # (squares per side n, Newton steps timed); K = n/2 as in the workload
+REFERENCE_SAMPLES = [(12, 1), (16, 1), (20, 1)]  # lighter: one Newton step per size for each reference-arm step
 WORKLOAD_NEWTON_STEPS = 49            # Newton steps of the GPU solve of this workload (same mu schedule)
 
 
@@ -168,12 +168,15 @@ def oracle_newton_seconds(threads: int, samples=ORACLE_SAMPLES) -> list:
             "    n, K, r0, r1 = config_densities('mixN', n)\n"
             "    d = ipm.discretise(n, K)\n"
             "    phi, rho, s = ipm.initial_point(d, r0, r1, 1.0)\n"
-            "    t = time.perf_counter()\n"
+            "    best = None\n"
             "    for _ in range(steps):\n"
+            "        t = time.perf_counter()\n"
             "        dphi, drho, ds, _ = ipm.newton_direction(d, phi, rho, s, r0, r1, 1.0)\n"
             "        a = min(ipm.step_length(rho, drho, 0.99), ipm.step_length(s, ds, 0.99))\n"
             "        phi, rho, s = phi + a * dphi, ipm.renormalise(d, rho + a * drho, r0), s + a * ds\n"
-            "    out.append((n, K, (time.perf_counter() - t) / steps))\n"
+            "        el = time.perf_counter() - t\n"
+            "        best = el if best is None else min(best, el)\n"
+            "    out.append((n, K, best))\n"
             "print(json.dumps(out))\n") % (ROOT, list(samples))
     t = str(threads)
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
@@ -183,17 +186,21 @@ def oracle_newton_seconds(threads: int, samples=ORACLE_SAMPLES) -> list:
 
 def oracle_baseline(threads: int, newton_steps: int = WORKLOAD_NEWTON_STEPS, samples=ORACLE_SAMPLES) -> dict:
     """Extrapolated oracle time to solution of the workload from the sample sizes."""
-    pts = oracle_newton_seconds(threads, samples)
-    (n1, k1, t1), (n2, k2, t2) = pts[0], pts[-1]
-    u1, u2, uw = unknowns(n1, k1), unknowns(n2, k2), unknowns(WORKLOAD_N, WORKLOAD_K)
     import math
 
-    p = math.log(t2 / t1) / math.log(u2 / u1)
-    per_step = t2 * (uw / u2) ** p
+    pts = oracle_newton_seconds(threads, samples)
+    # least-squares line through (log unknowns, log seconds per Newton step)
+    xs = [math.log(unknowns(n, k)) for n, k, _ in pts]
+    ys = [math.log(t) for _, _, t in pts]
+    xm, ym = sum(xs) / len(xs), sum(ys) / len(ys)
+    p = sum((x - xm) * (y - ym) for x, y in zip(xs, ys)) / sum((x - xm) ** 2 for x in xs)
+    uw = unknowns(WORKLOAD_N, WORKLOAD_K)
+    per_step = math.exp(ym + p * (math.log(uw) - xm))
     sample = (f"oracle IPM (exact sparse-LU Newton steps, as it stands) on the workload's density recipe "
               f"(3-Gaussian mixtures, seeds 2/3, floor 1e-4) at "
               + ", ".join(f"{n}x{n}, K={k}: {t:.3f} s per Newton step" for n, k, t in pts)
-              + f"; per-step time grows as unknowns^{p:.2f}; extrapolated to 64x64, K=32 "
+              + f" (fastest of the timed steps); least-squares fit: per-step time grows as unknowns^{p:.2f}; "
+                f"extrapolated to 64x64, K=32 "
                 f"({uw} unknowns): {per_step:.1f} s per Newton step x {newton_steps} Newton steps")
     import platform
     return {"value": per_step * newton_steps, "unit": "s", "cores": threads, "kind": "oracle",

@@ -39,7 +39,7 @@ def test_reference_arm_prints_one_line_with_the_workload_config(monkeypatch, cap
     the same metric, unit and config as the GPU arm, and nothing on other ranks."""
     import json
 
-    # per-step times (n=16, n=24) of three runs: warm-up, then two timed steps
+    # per-step times (n=16, n=24) of three runs: warm-up, then two timed steps, then the all-cores run
     runs = iter([[(16, 8, 9.0), (24, 12, 90.0)], [(16, 8, 1.0), (24, 12, 10.0)], [(16, 8, 1.0), (24, 12, 10.0)],
                  [(16, 8, 0.5), (24, 12, 5.0)]])
     monkeypatch.setattr(bench, "oracle_newton_seconds", lambda threads, samples=None: next(runs))
@@ -60,6 +60,18 @@ def test_reference_arm_prints_one_line_with_the_workload_config(monkeypatch, cap
     assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     bench.run_reference(_args(), 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_baseline_fit_over_three_sizes(monkeypatch):
+    """Three sample sizes on an exact power law t = a u^2 give p = 2 and the power law's value at
+    the workload's unknown count."""
+    u = bench.unknowns
+    pts = [(n, n // 2, 1e-9 * u(n, n // 2) ** 2) for n in (12, 18, 24)]
+    monkeypatch.setattr(bench, "oracle_newton_seconds", lambda threads, samples=None: pts)
+    b = bench.oracle_baseline(1, newton_steps=10)
+    assert abs(b["growth_exponent"] - 2.0) < 1e-9
+    assert abs(b["per_newton_step_s"] - 1e-9 * u(64, 32) ** 2) < 1e-6 * b["per_newton_step_s"]
+    assert abs(b["value"] - 10 * b["per_newton_step_s"]) < 1e-9 * b["value"]
 
 
 def test_unknowns_of_the_newton_system():
