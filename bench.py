@@ -60,6 +60,7 @@ def parse_args():
     p.add_argument("--batched-streams", type=int, default=16)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-stress", action="store_true", help="skip the 256x256, K=64 roofline leg")
+    p.add_argument("--no-tune", action="store_true", help="skip the autotuner run")
     return p.parse_args()
 
 
@@ -372,6 +373,19 @@ def run_ours(args, world, rank, local):
                              for g in sorted(sprof, key=lambda g: -sprof[g][0]) if sprof[g][1] > 0}}
         del smesh
 
+    # the autotuner at the final (smallest-mu) state of the solve, where most Newton steps are spent,
+    # then one full solve with the settings it picks (reported beside the default settings' time)
+    tuned = None
+    if rank == 0 and not args.no_tune:
+        topt, tsec = capi.ot_tune_newton(mesh, K, res["stats"]["mu"], res["phi"], res["rho"], res["s"], r0d, r1d,
+                                         options=capi.default_options(precision=args.precision))
+        tms, tres, _ = timed_solves(1, 1, topt)
+        tuned = {"smooth_sweeps": topt.smooth_sweeps, "coarse_sweeps": topt.coarse_sweeps,
+                 "lap_cycles": topt.lap_cycles, "candidates": [list(c) for c in capi.TUNE_GRID],
+                 "newton_seconds": tsec, "solve_seconds": tms[0] / 1e3,
+                 "newton_steps": tres["stats"]["newton_steps"], "fgmres_iters": tres["stats"]["fgmres_iters"],
+                 "cost_rel_diff": abs(tres["cost"] - res["cost"]) / abs(res["cost"])}
+
     # 5. the batched workload: 64 independent problems of uneven size on concurrent streams
     batched = None
     if not args.no_batched:
@@ -435,6 +449,7 @@ def run_ours(args, world, rank, local):
         "roofline": roofline,
         "roofline_groups": roofline_groups,
         "stress256": stress,
+        "tuned": tuned,
         "kernel_share_ms_per_solve": {k: v[0] for k, v in prof_all.items()},
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -183,7 +183,10 @@ ot_status ot_newton_solve(ot_mesh* mesh, int32_t K, double mu, const double* phi
  * converged point (phi, rho, s) of the barrier problem with parameter mu:
  * one adjoint solve with the transposed Jacobian, which after eliminating ds
  * is the same symmetric saddle operator, preconditioned by BB.  Outputs
- * grad_in, grad_f (N' each). */
+ * grad_in, grad_f (N' each).  Only mass-preserving perturbations of the
+ * densities are admissible (their masses must stay equal), so each gradient
+ * is defined up to a multiple of the cell areas |c'|; it is returned in the
+ * area gauge, with that component removed (|c'| . grad = 0). */
 ot_status ot_cost_grad(ot_mesh* mesh, int32_t K, double mu, const double* phi, const double* rho,
                        const double* s, const double* rho_in, const double* rho_f, const ot_options* opt,
                        double* grad_in, double* grad_f, void* cuda_stream);

@@ -11,17 +11,12 @@ times the incoming gradient.
 
 The masses of rho_in and rho_f must stay equal, so only mass-preserving
 perturbations are admissible and each gradient is defined up to a multiple of
-the coarse cell areas |c'|; the gradients are returned with that component
-removed (least squares).
+the coarse cell areas |c'|; ot_cost_grad returns the representative with that
+component removed (the area gauge).
 """
 import torch
 
 from . import capi
-
-
-def _area_gauge(g: torch.Tensor, areas: torch.Tensor) -> torch.Tensor:
-    a = areas.to(device=g.device, dtype=g.dtype)
-    return g - (torch.dot(a, g) / torch.dot(a, a)) * a
 
 
 class TransportCost(torch.autograd.Function):
@@ -38,9 +33,7 @@ class TransportCost(torch.autograd.Function):
     def backward(ctx, grad_out):
         r0, r1, phi, rho, s = ctx.saved_tensors
         gin, gf = capi.ot_cost_grad(ctx.mesh, ctx.K, ctx.mu, phi, rho, s, r0, r1, options=ctx.options)
-        gin = _area_gauge(gin, ctx.mesh.coarse_areas) * grad_out
-        gf = _area_gauge(gf, ctx.mesh.coarse_areas) * grad_out
-        return gin, gf, None, None, None, None, None
+        return gin * grad_out, gf * grad_out, None, None, None, None, None
 
 
 def transport_cost(mesh, rho_in, rho_f, K: int, mu0: float = 1.0, tol: float = 1e-6, options=None):

@@ -402,6 +402,10 @@ ot_status ot_cost_grad(ot_mesh* mesh, int32_t K, double mu, const double* phi, c
   ot::fgmres(W, o, W.rhs, W.sol, eps, W.scal + 40, 1, st);
   ot::recover_direction(W, st);
   ot::k_adjoint_grad(W.d, W.phi, W.sol, W.u, W.u + W.d.Nc, st);
+  // area gauge: the component along |c'| removed from each gradient (all |c'| are equal on
+  // this mesh, so that is the mean of each of the two N'-vectors)
+  ot::k_slice_sums(W.u, 2, W.d.Nc, 1.0 / (double)W.d.Nc, W.scal + 48, st);
+  ot::k_slice_shift(W.u, 2, W.d.Nc, W.scal + 48, 1.0, st);
   copy_out(grad_in, W.u, W.d.Nc, o, st);
   copy_out(grad_f, W.u + W.d.Nc, W.d.Nc, o, st);
   dev::sync(st);
