@@ -250,6 +250,52 @@ __device__ __forceinline__ T sweep_neighbour(const LevelView<T>& L, const LevelV
   return v;
 }
 
+// The same on a staged level with tables (32-bit indices): the parent of the
+// neighbour from the table.
+template <typename T, int MODE>
+__device__ __forceinline__ T sweep_neighbour_t(const LevelView<T>& L, const LevelView<T>& Lc, int k, int o) {
+  if (MODE == kSweepFromZero) return (T)0;
+  T v = L.x[k * (int)L.ld + o];
+  if (MODE == kSweepAfterProlong) v += Lc.x[k * (int)Lc.ld + L.par[o]];
+  return v;
+}
+
+// level_apply on a staged level with tables.
+template <typename T>
+__device__ __forceinline__ T level_apply_t(int S, const LevelView<T>& L, int k, int c) {
+  const int ld = (int)L.ld, nc = (int)L.nc;
+  const T* xs = L.x + k * ld;
+  const T xc = xs[c];
+  T acc = 0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    const int o = L.nbt[sl * nc + c];
+    if (o < 0) continue;
+    acc += L.alpha[(sl * S + k) * ld + c] * (xc - xs[o]);
+  }
+  if (L.tau) {
+    const T xm = (k > 0) ? L.x[(k - 1) * ld + c] : (T)0;
+    const T xp = (k < S - 1) ? L.x[(k + 1) * ld + c] : (T)0;
+    acc += L.tau[k * ld + c] * (2 * xc - xm - xp);
+  }
+  return acc;
+}
+
+// Point update of cell c in slice k of a staged level with tables (point_gs / point_gs_mode).
+template <typename T, int MODE>
+__device__ __forceinline__ void point_gs_t(int S, const LevelView<T>& L, const LevelView<T>& Lc, int k, int c) {
+  const int ld = (int)L.ld, nc = (int)L.nc;
+  T num = L.b[k * ld + c], den = 0;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    const T a = L.alpha[(sl * S + k) * ld + c];
+    den += a;
+    const int o = L.nbt[sl * nc + c];
+    if (MODE != kSweepFromZero && o >= 0) num += a * sweep_neighbour_t<T, MODE>(L, Lc, k, o);
+  }
+  L.x[k * ld + c] = mg_div(num, den);
+}
+
 // Line update of cell c (same system as line_gs) by one warp; neighbour
 // values as the sweep mode gives them.
 template <typename T, int KPL, int MODE>
@@ -903,11 +949,19 @@ __device__ __forceinline__ void line_factor(int S, const LevelView<T>& L, int c)
 template <typename T, int KPL, int MODE>
 __device__ __forceinline__ void line_scan_solve(int S, const LevelView<T>& L, const LevelView<T>& Lc, int c,
                                                 int lane) {
-  i64 nb[3];
-  neighbours(L.m, decode(L.m, c), nb);
-  const i64 ld = L.ld;
+  int nb[3];
+  if (L.nbt) {
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) nb[sl] = L.nbt[sl * (int)L.nc + c];
+  } else {
+    i64 nl[3];
+    neighbours(L.m, decode(L.m, c), nl);
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) nb[sl] = (int)nl[sl];
+  }
+  const int ld = (int)L.ld;
   const T* inv = L.fac;
-  const T* cp = L.fac + (i64)S * ld;
+  const T* cp = L.fac + S * ld;
   T A[KPL], B[KPL], C[KPL];
 #pragma unroll
   for (int q = 0; q < KPL; ++q) {
@@ -916,12 +970,14 @@ __device__ __forceinline__ void line_scan_solve(int S, const LevelView<T>& L, co
     B[q] = 0;
     C[q] = 0;
     if (k < S) {
-      const i64 o = (i64)k * ld + c;
+      const int o = k * ld + c;
       T rhs = L.b[o];
       if (MODE != kSweepFromZero) {
 #pragma unroll
         for (int sl = 0; sl < 3; ++sl)
-          if (nb[sl] >= 0) rhs += L.alpha[((i64)sl * S + k) * ld + c] * sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
+          if (nb[sl] >= 0)
+            rhs += L.alpha[(sl * S + k) * ld + c] *
+                   (L.par ? sweep_neighbour_t<T, MODE>(L, Lc, k, nb[sl]) : sweep_neighbour<T, MODE>(L, Lc, k, nb[sl]));
       }
       const T iv = inv[o];
       A[q] = (k > 0) ? L.tau[o] * iv : (T)0;
@@ -933,7 +989,7 @@ __device__ __forceinline__ void line_scan_solve(int S, const LevelView<T>& L, co
 #pragma unroll
   for (int q = 0; q < KPL; ++q) {
     const int k = lane * KPL + q;
-    if (k < S) L.x[(i64)k * ld + c] = B[q];
+    if (k < S) L.x[k * ld + c] = B[q];
   }
 }
 
@@ -1127,8 +1183,41 @@ __device__ void stage_levels(const LevelSet<T>& g, LevelSet<T>& s, T* smem, int 
         p += 2 * n1;
       }
     }
+    if (g.L[g.n - 1].tau) p += 4 * S_view;  // the aggregate scratch after the last level (sch_lower_body)
+    int* q = reinterpret_cast<int*>(p);
+    for (int l = 0; l < g.n; ++l) {
+      LevelView<T>& V = s.L[l];
+      const int nc = (int)V.nc;
+      V.nbt = q;
+      V.par = q + 3 * nc;
+      V.chd = q + 4 * nc;
+      q += 8 * nc;
+    }
   }
   __syncthreads();
+  // neighbour, parent and child tables of every staged level (one pass over all cells)
+  {
+    int total = 0;
+    for (int l = 0; l < g.n; ++l) total += (int)s.L[l].nc;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      int l = 0, c = i;
+      while (c >= (int)s.L[l].nc) c -= (int)s.L[l++].nc;
+      const LevelView<T>& V = s.L[l];
+      const int nc = (int)V.nc;
+      const Cell q = decode(V.m, c);
+      i64 nb[3];
+      neighbours(V.m, q, nb);
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) V.nbt[sl * nc + c] = (int)nb[sl];
+      V.par[c] = (l + 1 < g.n) ? (int)parent(V.m, q) : -1;
+      if (l > 0) {
+        i64 ch[4];
+        children(V.m, q, ch);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) V.chd[a * nc + c] = (int)ch[a];
+      }
+    }
+  }
   for (int l = 0; l < g.n; ++l) {
     const LevelView<T>& G = g.L[l];
     const LevelView<T>& V = s.L[l];
@@ -1156,7 +1245,9 @@ template <typename T>
 size_t fused_smem_bytes(const LevelView<T>* lv, int nlev, int S_view, bool tc) {
   size_t cells = 0;
   for (int l = 0; l < nlev; ++l) cells += (size_t)S_view * (size_t)staged_ld(lv[l].nc, S_view);
-  return sizeof(T) * cells * (tc ? 9 : 6) + (tc ? sizeof(T) * 4 * (size_t)S_view : 0);
+  size_t tables = 0;  // neighbour, parent and child tables: 8 ints per cell of every level
+  for (int l = 0; l < nlev; ++l) tables += 8 * sizeof(int) * (size_t)lv[l].nc;
+  return sizeof(T) * cells * (tc ? 9 : 6) + (tc ? sizeof(T) * 4 * (size_t)S_view : 0) + tables;
 }
 
 // Slice Laplacians: one CTA per slice (blockIdx.x), point red-black GS, the
@@ -1182,20 +1273,22 @@ __global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, Le
     for (int it = 0; it < sweeps; ++it)
       for (int col = 0; col < 2; ++col) {
         if (it == 0 && col == 0)
-          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_mode<T, kSweepFromZero>(1, L, L, 0, i);
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_t<T, kSweepFromZero>(1, L, L, 0, i);
         else
-          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_t<T, kSweepPlain>(1, L, L, 0, col * sq + i);
         __syncthreads();
       }
     if (l == last) break;
     // b_coarse = J^T (b - M x) in one phase
     const LevelView<T>& Lc = ls.L[l + 1];
-    for (int C = threadIdx.x; C < (int)Lc.nc; C += blockDim.x) {
-      i64 ch[4];
-      children(Lc.m, decode(Lc.m, C), ch);
+    const int ncc = (int)Lc.nc;
+    for (int C = threadIdx.x; C < ncc; C += blockDim.x) {
       T acc = 0;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) acc += L.b[ch[a]] - level_apply(1, L, 0, ch[a]);
+      for (int a = 0; a < 4; ++a) {
+        const int ch = Lc.chd[a * ncc + C];
+        acc += L.b[ch] - level_apply_t(1, L, 0, ch);
+      }
       Lc.b[C] = acc;
     }
     __syncthreads();
@@ -1205,15 +1298,15 @@ __global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, Le
     const LevelView<T>& Lc = ls.L[l + 1];
     const int sq = L.m * L.m, nc = (int)L.nc;
     if (nu == 0) {
-      for (int c = threadIdx.x; c < nc; c += blockDim.x) L.x[c] += Lc.x[parent_of(L.m, c)];
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) L.x[c] += Lc.x[L.par[c]];
       __syncthreads();
     }
     for (int it = 0; it < nu; ++it)
       for (int col = 1; col >= 0; --col) {
         if (it == 0 && col == 1)
-          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_mode<T, kSweepAfterProlong>(1, L, Lc, 0, sq + i);
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_t<T, kSweepAfterProlong>(1, L, Lc, 0, sq + i);
         else
-          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs(1, L, 0, (i64)(col * sq + i));
+          for (int i = threadIdx.x; i < sq; i += blockDim.x) point_gs_t<T, kSweepPlain>(1, L, L, 0, col * sq + i);
         __syncthreads();
       }
   }
@@ -1261,13 +1354,15 @@ __device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, u
     // b_coarse = J^T (b - M x) in one phase
     const LevelView<T>& Lc = ls.L[l + 1];
     const int ldc = (int)Lc.ld;
-    for (SliceWalk w((int)Lc.nc); w.k < S; w.next()) {
-      i64 ch[4];
-      children(Lc.m, decode(Lc.m, w.c), ch);
+    const int ncc = (int)Lc.nc;
+    for (SliceWalk w(ncc); w.k < S; w.next()) {
       const T* bf = L.b + w.k * ld;
       T acc = 0;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) acc += bf[ch[a]] - level_apply(S, L, w.k, ch[a]);
+      for (int a = 0; a < 4; ++a) {
+        const int ch = Lc.chd[a * ncc + w.c];
+        acc += bf[ch] - level_apply_t(S, L, w.k, ch);
+      }
       Lc.b[w.k * ldc + w.c] = acc;
     }
     __syncthreads();
@@ -1279,7 +1374,7 @@ __device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, u
     const LevelView<T>& Lc = ls.L[l + 1];
     const int sq = L.m * L.m, nc = (int)L.nc, ld = (int)L.ld, ldc = (int)Lc.ld;
     if (nu == 0) {
-      for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] += Lc.x[w.k * ldc + (int)parent_of(L.m, w.c)];
+      for (SliceWalk w(nc); w.k < S; w.next()) L.x[w.k * ld + w.c] += Lc.x[w.k * ldc + L.par[w.c]];
       __syncthreads();
     }
     for (int it = 0; it < nu; ++it)

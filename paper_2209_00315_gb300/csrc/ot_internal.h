@@ -328,6 +328,14 @@ struct LevelView {
   // fused levels (factored at the start of each fused cycle); nullptr elsewhere.
   // The line systems change once per Newton step; every sweep only substitutes.
   T* fac = nullptr;
+  // Shared-memory copies of the fused levels only: per cell its three
+  // neighbours (-1 on the boundary) [3][nc], its parent on the next coarser
+  // level [nc] (-1 on the coarsest), its four children on the next finer level
+  // [4][nc] (level 0: unused); built once per fused launch, so that sweeps and
+  // transfers index with 32-bit loads instead of decoding cell numbers.
+  int* nbt = nullptr;
+  int* par = nullptr;
+  int* chd = nullptr;
 };
 
 template <typename T>

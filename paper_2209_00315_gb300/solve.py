@@ -20,6 +20,10 @@ from . import capi
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--workload", default="mix64")
+    p.add_argument("--n", type=int, default=None, help="squares per side for --workload mixN (K = n/2)")
+    p.add_argument("--max-newton", type=int, default=None, help="Newton steps per barrier stage")
+    p.add_argument("--allow-unconverged", action="store_true",
+                   help="report a Newton or FGMRES cap as a result (exit 0), e.g. to profile a few capped steps")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--repeat", type=int, default=1)
     p.add_argument("--tol", type=float, default=1e-6, help="duality-gap target")
@@ -35,7 +39,7 @@ def main(argv=None):
 
     from ot_inputs import config_densities
 
-    n, K, r0, r1 = config_densities(a.workload)
+    n, K, r0, r1 = config_densities(a.workload, a.n) if a.workload == "mixN" else config_densities(a.workload)
     mesh = capi.Mesh(n)
     r0d = torch.from_numpy(r0).cuda()
     r1d = torch.from_numpy(r1).cuda()
@@ -50,12 +54,21 @@ def main(argv=None):
         extra["graphs"] = a.graphs
     if a.gs_shadow is not None:
         extra["gs_shadow"] = a.gs_shadow
+    if a.max_newton is not None:
+        extra["max_newton"] = a.max_newton
     opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
     walls, res = [], None
     for _ in range(a.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = capi.ot_ipm_solve(mesh, r0d, r1d, K, tol=a.tol, options=opt)
+        try:
+            res = capi.ot_ipm_solve(mesh, r0d, r1d, K, tol=a.tol, options=opt)
+        except capi.OTError as e:
+            if not (a.allow_unconverged and e.code == 4):
+                raise
+            torch.cuda.synchronize()
+            print(json.dumps({"workload": a.workload, "n": n, "K": K, "stopped": str(e)}))
+            return
         torch.cuda.synchronize()
         walls.append(time.perf_counter() - t0)
     st = res["stats"]
