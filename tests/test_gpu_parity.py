@@ -87,18 +87,29 @@ def test_schur_operator_matches_oracle(cases):
         assert rel(out, S @ z) < 1e-13, (n, K)
 
 
-@pytest.mark.parametrize("n,K", [(2, 2), (4, 3)])
-def test_bb_application_matches_exact_oracle(gpu_lib, n, K):
+@pytest.mark.parametrize("n,K,phi_kind", [(2, 2, "random"), (4, 3, "random"), (32, 2, "smooth")])
+def test_bb_application_matches_exact_oracle(gpu_lib, n, K, phi_kind):
     """One application of the BB preconditioner (Sec. 4.3.3) in FP64 with the inner
     Schur GMRES driven to 1e-13 and 60 V-cycles per slice Laplacian, against the
     oracle's application with sparse-LU solves.  x is compared after removing each
-    slice's mean, the constant that the singular slice Laplacians leave free."""
+    slice's mean, the constant that the singular slice Laplacians leave free.  At
+    n = 32 (8192 cells per slice) the finest Laplacian level is swept in device
+    memory and the coarser ones in shared memory; below, all in shared memory.
+    The large case takes a smooth phi: cell-wise random potentials have gradients
+    growing as 1/h, which makes the Schur block indefinite from n = 8 on (real
+    parts of its eigenvalues down to -89 at n = 16) and no longer a state the
+    interior-point method visits."""
     from paper_2209_00315_gb300 import capi
     from oracle import operators as ops
 
     d = ipm.discretise(n, K)
     phi, rho, s, r0, r1 = random_state(d, 7 * n + K)
-    phi = 0.1 * phi
+    if phi_kind == "smooth":
+        c = d.t.fine.centre
+        wave = np.sin(2 * np.pi * c[:, 0]) * np.cos(np.pi * c[:, 1])
+        phi = np.concatenate([0.1 * wave * (k / K) for k in range(K + 1)])
+    else:
+        phi = 0.1 * phi
     Np = (K + 1) * d.N
     v = np.random.default_rng(5).standard_normal(Np + K * d.Nc)
     x, y = ops.bb_apply_exact(d, phi, rho, s, r0, r1, v)
