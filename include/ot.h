@@ -67,6 +67,10 @@ typedef struct ot_mesh ot_mesh;  /* opaque, library-owned */
 
 typedef enum { OT_MEM_DEVICE = 0, OT_MEM_HOST = 1 } ot_memspace;
 typedef enum { OT_PREC_FP64 = 0, OT_PREC_MIXED = 1 } ot_precision;
+/* Preconditioner of the outer FGMRES (Sec. 4.2-4.3): BB (the default); SIMPLE;
+ * or HYBRID: SIMPLE in the barrier stages with mu < simple_mu, BB before them
+ * (the switch the paper proposes for small mu, where BB degrades). */
+typedef enum { OT_PRECOND_BB = 0, OT_PRECOND_SIMPLE = 1, OT_PRECOND_HYBRID = 2 } ot_precond;
 
 /* Solver options; ot_default_options() fills the values used by the paper. */
 typedef struct {
@@ -99,6 +103,11 @@ typedef struct {
                                conditional (WHILE) nodes driven by device-side convergence tests;
                                0: the same kernels launched one by one, the host reading the
                                convergence state after every Krylov step */
+  int32_t precond;          /* ot_precond: OT_PRECOND_BB (default), OT_PRECOND_SIMPLE or OT_PRECOND_HYBRID.
+                               SIMPLE runs in FP64 in both precisions: A^ = Diag(A), its Schur complement
+                               solved by GMRES to eps_schur (at most schur_max_iter iterations),
+                               preconditioned by exact solves of its time-line (tridiagonal) part */
+  double simple_mu;         /* HYBRID: SIMPLE for the stages with mu < simple_mu (1e-5) */
 } ot_options;
 
 #define OT_MAX_STAGES 40
@@ -262,6 +271,19 @@ ot_status ot_schur_apply(ot_mesh* mesh, int32_t K, const double* phi, const doub
 ot_status ot_bb_apply(ot_mesh* mesh, int32_t K, const ot_options* opt, const double* phi, const double* rho,
                       const double* s, const double* rho_in, const double* rho_f, const double* v, double* out,
                       void* cuda_stream);
+
+/* One application of the SIMPLE preconditioner (Sec. 4.2) to the projected
+ * system with A^ = Diag(A): given v = (c; d) (device FP64, (K+1) N + K N'),
+ * returns out = (x; y) with
+ *   x1 = A^-1 c,  y ~= S^-1 (d - P B x1),  x = x1 - A^-1 B^T P^T y,
+ *   S^ = -(P C P^T + P B A^-1 B^T P^T),
+ * y in the range of P^T (zero slice means), the Schur solve by GMRES to
+ * opt->eps_schur relative residual within opt->schur_max_iter iterations.  At
+ * the state (phi, rho, s) (device FP64).  The library allocates and keeps the
+ * SIMPLE workspace on first use with this mesh and K. */
+ot_status ot_simple_apply(ot_mesh* mesh, int32_t K, const ot_options* opt, const double* phi, const double* rho,
+                          const double* s, const double* rho_in, const double* rho_f, const double* v, double* out,
+                          void* cuda_stream);
 
 /* Discrete cost C and dual value D (host outputs, nullable). */
 ot_status ot_cost_dual(ot_mesh* mesh, int32_t K, const double* phi, const double* rho, const double* rho_in,

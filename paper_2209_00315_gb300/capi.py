@@ -23,12 +23,14 @@ STATUS = {0: "OT_OK", 1: "OT_ERR_INVALID_ARG", 2: "OT_ERR_MASS_MISMATCH", 3: "OT
           4: "OT_ERR_NOT_CONVERGED", 5: "OT_ERR_BREAKDOWN", 6: "OT_ERR_NONFINITE", 7: "OT_ERR_CUDA", 8: "OT_ERR_OOM"}
 OT_MEM_DEVICE, OT_MEM_HOST = 0, 1
 OT_PREC_FP64, OT_PREC_MIXED = 0, 1
+OT_PRECOND_BB, OT_PRECOND_SIMPLE, OT_PRECOND_HYBRID = 0, 1, 2
 OT_MAX_STAGES = 40
 
 EXPORTED = ["ot_default_options", "ot_mesh_create", "ot_mesh_destroy", "ot_mesh_info", "ot_ipm_solve",
             "ot_ipm_solve_batched", "ot_newton_solve", "ot_cost_grad", "ot_last_error", "ot_residual", "ot_kkt_apply", "ot_schur_apply",
             "ot_bb_apply", "ot_cost_dual", "ot_kernel_timing_enable", "ot_kernel_timing_count",
-            "ot_kernel_timing_read", "ot_kernel_launches", "ot_kkt_apply_noalloc", "ot_tune_newton"]
+            "ot_kernel_timing_read", "ot_kernel_launches", "ot_kkt_apply_noalloc", "ot_tune_newton",
+            "ot_simple_apply"]
 
 
 class OTError(RuntimeError):
@@ -48,7 +50,7 @@ class ot_options(C.Structure):
                 ("fgmres_restart", C.c_int32), ("fgmres_max_iter", C.c_int32), ("schur_max_iter", C.c_int32),
                 ("lap_cycles", C.c_int32), ("smooth_sweeps", C.c_int32), ("coarse_sweeps", C.c_int32),
                 ("max_newton", C.c_int32), ("verbose", C.c_int32), ("gs_shadow", C.c_int32),
-                ("graphs", C.c_int32)]
+                ("graphs", C.c_int32), ("precond", C.c_int32), ("simple_mu", C.c_double)]
 
 
 class ot_stats(C.Structure):
@@ -104,6 +106,7 @@ def load():
         "ot_schur_apply": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
         "ot_kkt_apply_noalloc": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_bb_apply": (_I, [_P, _I, C.POINTER(ot_options), _P, _P, _P, _P, _P, _P, _P, _P]),
+        "ot_simple_apply": (_I, [_P, _I, C.POINTER(ot_options), _P, _P, _P, _P, _P, _P, _P, _P]),
         "ot_cost_dual": (_I, [_P, _I, _P, _P, _P, _P, C.POINTER(_D), C.POINTER(_D), _P]),
         "ot_kernel_timing_enable": (None, [_I, _I]),
         "ot_kernel_timing_count": (_I, []),
@@ -131,6 +134,8 @@ def default_options(**overrides) -> ot_options:
     for k, v in overrides.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": OT_PREC_FP64, "mixed": OT_PREC_MIXED}[v]
+        if k == "precond" and isinstance(v, str):
+            v = {"bb": OT_PRECOND_BB, "simple": OT_PRECOND_SIMPLE, "hybrid": OT_PRECOND_HYBRID}[v]
         setattr(o, k, v)
     return o
 
@@ -346,6 +351,15 @@ def ot_schur_apply(mesh: Mesh, K: int, phi, rho, s, z, stream=None):
     out = torch.empty_like(z)
     _check(load().ot_schur_apply(mesh.handle, int(K), _dev_ptr(phi), _dev_ptr(rho), _dev_ptr(s), _dev_ptr(z),
                                  _dev_ptr(out), _stream(stream)))
+    return out
+
+
+def ot_simple_apply(mesh: Mesh, K: int, phi, rho, s, rho_in, rho_f, v, options=None, stream=None):
+    """One SIMPLE preconditioner application (Sec. 4.2) at (phi, rho, s): returns (x; y)."""
+    o = options if options is not None else default_options()
+    out = torch.empty_like(v)
+    _check(load().ot_simple_apply(mesh.handle, int(K), C.byref(o), _dev_ptr(phi), _dev_ptr(rho), _dev_ptr(s),
+                                  _dev_ptr(rho_in), _dev_ptr(rho_f), _dev_ptr(v), _dev_ptr(out), _stream(stream)))
     return out
 
 

@@ -75,6 +75,8 @@ void ot_default_options(ot_options* o) {
   o->verbose = 0;
   o->gs_shadow = 1;
   o->graphs = 1;
+  o->precond = OT_PRECOND_BB;
+  o->simple_mu = 1e-5;
 }
 
 const char* ot_last_error(void) { return g_err.c_str(); }
@@ -106,6 +108,9 @@ static ot_options resolve(const ot_options* o) {
   require(r.max_newton >= 1, "options.max_newton");
   require(r.gs_shadow == 0 || r.gs_shadow == 1, "options.gs_shadow must be 0 or 1");
   require(r.graphs == 0 || r.graphs == 1, "options.graphs must be 0 or 1");
+  require(r.precond == OT_PRECOND_BB || r.precond == OT_PRECOND_SIMPLE || r.precond == OT_PRECOND_HYBRID,
+          "options.precond must be OT_PRECOND_BB, OT_PRECOND_SIMPLE or OT_PRECOND_HYBRID");
+  require(r.simple_mu >= 0 && std::isfinite(r.simple_mu), "options.simple_mu must be finite and >= 0");
   return r;
 }
 
@@ -361,6 +366,7 @@ ot_status ot_newton_solve(ot_mesh* mesh, int32_t K, double mu, const double* phi
   require_positive(W, W.rho, W.Nr, "rho", st);
   require_positive(W, W.s, W.Nr, "s", st);
   W.outer_iters = W.inner_iters = W.capped_solves = 0;
+  W.mu = mu;
   double t0 = dev::now();
   double f = ot::residual_norm(W, mu, st, nullptr);
   double eps = o.final_eps_out > 0 ? o.final_eps_out : o.eps_out;
@@ -393,6 +399,7 @@ ot_status ot_cost_grad(ot_mesh* mesh, int32_t K, double mu, const double* phi, c
   load_state(W, phi, rho, s, rho_in, rho_f, o, st);
   require_positive(W, W.rho, W.Nr, "rho", st);
   require_positive(W, W.s, W.Nr, "s", st);
+  W.mu = mu;
   // J^T lambda = dC/du reduces (eliminating lambda_s) to the symmetric saddle system (Sec. 3.1)
   ot::k_adjoint_rhs(W.d, W.phi, W.rho, W.r0, W.r1, W.rhs, W.gsum, st);
   ot::refresh_coefficients(W, st);
@@ -548,6 +555,24 @@ ot_status ot_schur_apply(ot_mesh* mesh, int32_t K, const double* phi, const doub
   Stream st = cuda_stream;
   Workspace& W = op_workspace(mesh, K);
   ot::k_schur_apply(W.d, phi, rho, s, z, out, W.u, st);
+  dev::sync(st);
+  return OT_OK;
+  OT_CATCH
+}
+
+ot_status ot_simple_apply(ot_mesh* mesh, int32_t K, const ot_options* opt_in, const double* phi, const double* rho,
+                          const double* s, const double* rho_in, const double* rho_f, const double* v, double* out,
+                          void* cuda_stream) {
+  OT_TRY
+  ot_options o = resolve(opt_in);
+  o.memspace = OT_MEM_DEVICE;
+  require(v && out, "NULL argument");
+  Stream st = cuda_stream;
+  Workspace& W = workspace(mesh, K, o);
+  load_state(W, phi, rho, s, rho_in, rho_f, o, st);
+  ot::refresh_coefficients(W, st);
+  ot::simple_prepare(W, st);
+  ot::simple_apply(W, o, v, out, st);
   dev::sync(st);
   return OT_OK;
   OT_CATCH

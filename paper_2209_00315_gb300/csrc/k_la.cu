@@ -47,7 +47,7 @@ long long n_acc[COUNT] = {0};
 double b_acc[COUNT] = {0};
 const char* names[COUNT] = {"kkt_apply", "gs_dot", "gs_update", "krylov_combine", "lap_smooth",
                             "schur_line_smooth", "mg_transfer", "schur_apply", "residual", "bt_apply",
-                            "lap_lower_cycle", "schur_lower_cycle"};
+                            "lap_lower_cycle", "schur_lower_cycle", "simple_line_solve"};
 cudaEvent_t get_event() {
   if (!pool.empty()) {
     cudaEvent_t e = pool.back();

@@ -131,6 +131,7 @@ enum Id {
   BT,            // B^T P^T y
   LAP_LOWER,     // fused small levels of a slice-Laplacian V-cycle (one launch)
   SCH_LOWER,     // fused small levels of a space-time Schur V-cycle (one launch)
+  SIMPLE_LINE,   // time-line solves preconditioning SIMPLE's Schur complement
   COUNT
 };
 extern bool enabled;        // any group on
@@ -290,6 +291,25 @@ void k_adjoint_rhs(const Dims& d, const double* phi, const double* rho, const do
                    double* rhs, double* gsum, Stream st);
 // grad_in, grad_f (N' each) from the adjoint potential lam ((K+1) x N).
 void k_adjoint_grad(const Dims& d, const double* phi, const double* lam, double* gin, double* gf, Stream st);
+// SIMPLE preconditioner pieces (k_simple.cu).  Ad ((K+1) N) = diagonal of the
+// potential block A from the KKT coefficients kc.
+void k_simple_diag(const Dims& d, const double* kc, double* Ad, Stream st);
+// Factors (inv, e: K x N' each) of the time-line tridiagonal systems that
+// precondition SIMPLE's Schur complement, from kc and Ad.
+void k_simple_line_factor(const Dims& d, const double* kc, const double* Ad, double* inv, double* e, Stream st);
+// z = L^-1 (r - shift), L the time-line tridiagonal systems per coarse cell;
+// shift (nullable, K) is subtracted slice by slice; r and z (K x N') may not alias.
+void k_simple_line_solve(const Dims& d, const double* inv, const double* e, const double* r, const double* shift,
+                         double* z, Stream st);
+// G = Y^T L^-1 Y (K x K, Y the slice indicators), Cholesky-factored in place
+// (lower, column-major); scratch: K x N'; *status set to 1 if a pivot is not positive.
+constexpr int kSimpleMaxK = 1024;
+void k_simple_gram(const Dims& d, const double* inv, const double* e, double* scratch, double* G, int* status,
+                   Stream st);
+// lam = G^-1 t from the factor of k_simple_gram (K <= kSimpleMaxK).
+void k_simple_gram_solve(int K, const double* L, const double* t, double* lam, Stream st);
+// out = beta * out + alpha * num / den (element-wise; beta = 0 ignores out's old values)
+void k_quot(const double* num, const double* den, double alpha, double* out, double beta, i64 n, Stream st);
 // FP32 versions of the Schur-side operators (mixed precision), same layouts.
 void k_bt_apply(const Dims& d, const float* phi, const float* yr, float* out_phi, float* yr_mean, Stream st);
 void k_schur_apply(const Dims& d, const float* phi, const float* rho, const float* s, const float* z, float* out,

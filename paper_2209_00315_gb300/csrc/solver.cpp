@@ -224,8 +224,11 @@ Workspace::Workspace(int n, int K, int prec, const ot_options& opt) {
 
 Workspace::~Workspace() {
   double* bufs[] = {phi, rho, s, r0, r1, Fphi, Frho, Fs, rhs, sol, ytmp, hvec, ds, gsum, wsum, cshift, xmean,
-                    mass, scal, partial, u, bphi, srhs, zeta, kcoef};
+                    mass, scal, partial, u, bphi, srhs, zeta, kcoef, sAd, sinv, se, skin, sG, slam};
   for (double* b : bufs) dev::release(b);
+  sAd = sinv = se = skin = sG = slam = nullptr;
+  dev::release(sstat);
+  sstat = nullptr;
   phi = rho = s = r0 = r1 = Fphi = Frho = Fs = rhs = sol = ytmp = hvec = ds = nullptr;
   gsum = wsum = cshift = xmean = mass = scal = partial = u = bphi = srhs = zeta = kcoef = nullptr;
   outer.release();
@@ -483,18 +486,101 @@ void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out,
     bb_apply_t(W, opt, W.lapd, W.schd, W.bbd, v, out, st);
 }
 
-// ------------------------------------------------------------------ FGMRES
-// Inner iterations so far (device counter of the inner solver).
-static long long inner_total(Workspace& W, Stream st) {
-  KrylovT<double>& Kd = W.inner;
-  KrylovT<float>& Kf = W.innerf;
-  kry::Ctl c;
-  if (W.precision == OT_PREC_MIXED) {
-    dev::read_ctl(Kf.ctl, &c, st);
-  } else {
-    dev::read_ctl(Kd.ctl, &c, st);
+// ------------------------------------------------------------------ SIMPLE
+bool use_simple(const ot_options& opt, double mu) {
+  return opt.precond == OT_PRECOND_SIMPLE || (opt.precond == OT_PRECOND_HYBRID && mu < opt.simple_mu);
+}
+
+void simple_prepare(Workspace& W, Stream st) {
+  const Dims& d = W.d;
+  if (d.K > kSimpleMaxK) throw Error(OT_ERR_INVALID_ARG, "the SIMPLE preconditioner needs K <= 1024");
+  if (!W.sAd) {
+    W.sAd = dalloc(W.Np);
+    W.sinv = dalloc(W.Nr);
+    W.se = dalloc(W.Nr);
+    W.skin = dalloc(W.ntot);
+    W.sG = dalloc((i64)d.K * d.K);
+    W.slam = dalloc(2 * (i64)d.K);
+    W.sstat = (int*)dev::alloc(sizeof(int));
   }
-  return c.total;
+  if (!W.inner.ctl) W.inner.build(W.cur_inner, W.Nr);  // the FP64 inner Krylov space (mixed precision)
+  k_simple_diag(d, W.kcoef, W.sAd, st);
+  k_simple_line_factor(d, W.kcoef, W.sAd, W.sinv, W.se, st);
+  dev::zero(W.sstat, sizeof(int), st);
+  k_simple_gram(d, W.sinv, W.se, W.ytmp, W.sG, W.sstat, st);
+  int bad = 0;
+  dev::copy_d2h(&bad, W.sstat, sizeof(int), st);
+  dev::sync(st);
+  if (bad) throw Error(OT_ERR_BREAKDOWN, "SIMPLE: the slice-sum system of the time-line preconditioner is not positive definite");
+}
+
+// Sec. 4.2 with A^ = Diag(A) on the projected system [A, B^T P^T; P B, -P C P^T]:
+//   x1 = A^-1 c;  solve -S^ y = P B x1 - d;  x = x1 - A^-1 B^T P^T y,
+// -S^ = P C P^T + P B A^-1 B^T P^T applied through the KKT kernels: B^T P^T z,
+// scaled by A^-1, enters the KKT operator with x_rho = -z, whose rho rows are then
+// P B A^-1 B^T P^T z + P C P^T z.  The Krylov vectors stay in the range of P
+// (zero slice sums); the preconditioner solves the time-line part exactly there.
+void simple_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st) {
+  const Dims& d = W.d;
+  const i64 Np = W.Np, Nr = W.Nr;
+  const double* c = v;
+  const double* dv = v + Np;
+  double* x = out;
+  double* y = out + Np;
+  double* kin = W.skin;
+  double* kout = W.ytmp;
+  // x1 = A^-1 c (kept in x); right-hand side P B x1 - d
+  k_quot(c, W.sAd, 1.0, x, 0.0, Np, st);
+  dev::copy_d2d(kin, x, sizeof(double) * (size_t)Np, st);
+  dev::zero(kin + Np, sizeof(double) * (size_t)Nr, st);
+  k_kkt_apply(d, W.kcoef, kin, kout, W.xmean, nullptr, st);
+  dev::copy_d2d(W.srhs, kout + Np, sizeof(double) * (size_t)Nr, st);
+  k_axpby(-1.0, dv, 1.0, W.srhs, Nr, st);
+  // GMRES on -S^ y = P B x1 - d, preconditioned by the time-line solves
+  KrylovT<double>& K = W.inner;
+  const int m = std::min(opt.schur_max_iter, K.mmax);
+  dev::zero(y, sizeof(double) * (size_t)Nr, st);
+  // z = L^-1 (r - Y lambda) with (Y^T L^-1 Y) lambda = Y^T L^-1 r: P L P^T z = r, Y^T z = 0
+  double* t = W.slam;
+  double* lam = W.slam + d.K;
+  OpFn<double> prec = [&](const double* in, double* o, Stream s) {
+    k_simple_line_solve(d, W.sinv, W.se, in, nullptr, o, s);
+    k_slice_sums(o, d.K, d.Nc, 1.0, t, s);
+    k_simple_gram_solve(d.K, W.sG, t, lam, s);
+    k_simple_line_solve(d, W.sinv, W.se, in, lam, o, s);
+  };
+  OpFn<double> op = [&](const double* in, double* o, Stream s) {
+    k_bt_apply(d, W.kcoef, in, W.u, W.xmean, s);
+    k_quot(W.u, W.sAd, 1.0, kin, 0.0, Np, s);
+    k_scale(in, -1.0, kin + Np, Nr, s);
+    k_kkt_apply(d, W.kcoef, kin, kout, W.xmean, nullptr, s);
+    dev::copy_d2d(o, kout + Np, sizeof(double) * (size_t)Nr, s);
+  };
+  auto start = [&](Stream s) {
+    kry_solve_init(K.ctl, nullptr, 0, 0.0, m, s);
+    dev::copy_d2d(K.w, W.srhs, sizeof(double) * (size_t)Nr, s);
+  };
+  gmres_cycle<double>(K, m, opt.eps_schur, start, prec, op, false, false, y, st);
+  // x = x1 - A^-1 B^T P^T y
+  k_bt_apply(d, W.kcoef, y, W.u, W.xmean, st);
+  k_quot(W.u, W.sAd, -1.0, x, 1.0, Np, st);
+}
+
+// ------------------------------------------------------------------ FGMRES
+// Inner iterations so far (device counters of the inner solvers: the FP32 one of
+// mixed-precision BB, the FP64 one of FP64 BB and of SIMPLE).
+static long long inner_total(Workspace& W, Stream st) {
+  long long t = 0;
+  kry::Ctl c;
+  if (W.innerf.ctl) {
+    dev::read_ctl(W.innerf.ctl, &c, st);
+    t += c.total;
+  }
+  if (W.inner.ctl) {
+    dev::read_ctl(W.inner.ctl, &c, st);
+    t += c.total;
+  }
+  return t;
 }
 
 double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, double tol_rel,
@@ -504,7 +590,14 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
   const bool shadow = opt.gs_shadow && K.V32 != nullptr;
   const bool fp32_reorth = shadow && tol_rel >= 1e-8;
   const int m = std::min(effective_restart(opt, n), K.mmax);
-  OpFn<double> prec = [&](const double* in, double* out, Stream s) { bb_apply(W, opt, in, out, s); };
+  const bool simple = use_simple(opt, W.mu);
+  if (simple) simple_prepare(W, st);
+  OpFn<double> prec = [&](const double* in, double* out, Stream s) {
+    if (simple)
+      simple_apply(W, opt, in, out, s);
+    else
+      bb_apply(W, opt, in, out, s);
+  };
   OpFn<double> op = [&](const double* in, double* out, Stream s) {
     k_kkt_apply(W.d, W.kcoef, in, out, W.xmean, nullptr, s);
   };
@@ -525,9 +618,9 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
     };
     if (opt.graphs) {
       char key[160];
-      snprintf(key, sizeof(key), "fgmres:%d:%d:%d:%d:%d:%d:%d:%.17g:%p:%p:%p:%d", (int)first, m, (int)shadow,
+      snprintf(key, sizeof(key), "fgmres:%d:%d:%d:%d:%d:%d:%d:%.17g:%p:%p:%p:%d:%d", (int)first, m, (int)shadow,
                (int)fp32_reorth, opt.smooth_sweeps, opt.coarse_sweeps, opt.lap_cycles, opt.eps_schur, (const void*)b,
-               (const void*)x, (const void*)tol_ref, opt.schur_max_iter);
+               (const void*)x, (const void*)tol_ref, opt.schur_max_iter, (int)simple);
       std::unique_ptr<dev::Graph>& gp = W.graphs[key];
       if (!gp) {
         gp.reset(new dev::Graph());
@@ -627,6 +720,7 @@ int ipm_run(Workspace& W, const ot_options& opt, double mu0, double tol, ot_stat
     double t0 = dev::now();
     long long o0 = W.outer_iters, i0 = W.inner_iters;
     double norms[3];
+    W.mu = mu;
     f = residual_norm(W, mu, st, norms);
     bool last = stage == n_stage - 1;
     double tolN = ((last && opt.final_newton_tol > 0) ? opt.final_newton_tol : opt.newton_tol) * std::max(1.0, f);

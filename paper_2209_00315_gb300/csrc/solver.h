@@ -100,6 +100,12 @@ struct Workspace {
   BBVectors<float> bbf;
   Hierarchy<float> lapf, schf;
   Hierarchy<double> lapd, schd;
+  // SIMPLE (allocated on first use): the diagonal of A, the time-line factors of
+  // its Schur complement's preconditioner, and a KKT input vector
+  double *sAd = nullptr, *sinv = nullptr, *se = nullptr, *skin = nullptr;
+  double *sG = nullptr, *slam = nullptr;  // Cholesky factor of Y^T L^-1 Y (K x K); 2 K scalars
+  int* sstat = nullptr;                   // factorisation status (device)
+  double mu = 1.0;            // barrier parameter of the Newton system being solved
   double* host = nullptr;     // pinned host scratch: [0, hoff) and [hoff, 2 hoff) Hessenberg columns, then 64 scalars
   int hoff = 0;
   // counters of the current call
@@ -125,6 +131,14 @@ int effective_restart(const ot_options& opt, i64 ntot);
 void refresh_coefficients(Workspace& W, Stream st);
 // One BB preconditioner application (Sec. 4.3): out = P_BB^{-1} v, both of length ntot.
 void bb_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st);
+// Whether the outer FGMRES at barrier parameter mu uses SIMPLE (opt.precond).
+bool use_simple(const ot_options& opt, double mu);
+// Allocate SIMPLE's workspace (first use; never inside a graph capture) and
+// compute its diagonal and line factors from the current KKT coefficients.
+void simple_prepare(Workspace& W, Stream st);
+// One SIMPLE application (Sec. 4.2): out = P_SIMPLE^{-1} v, both of length ntot
+// (after simple_prepare at the current coefficients).
+void simple_apply(Workspace& W, const ot_options& opt, const double* v, double* out, Stream st);
 // FGMRES on the projected system; x (ntot) receives the solution; stops at a
 // residual estimate <= tol_rel * sqrt(sum_{i < nref} tol_ref[i]) (device
 // scalars, squared norms); returns the final residual estimate.

@@ -35,11 +35,17 @@ def main(argv=None):
                    help="1: FGMRES cycles as captured CUDA graphs (default); 0: launches one by one")
     p.add_argument("--gs-shadow", type=int, choices=[0, 1], default=None,
                    help="1: Gram-Schmidt dots from the FP32 basis copy (default); 0: all FP64")
+    p.add_argument("--K", type=int, default=None, help="time steps, overriding the workload's K")
+    p.add_argument("--precond", choices=["bb", "simple", "hybrid"], default=None,
+                   help="outer preconditioner (default bb); hybrid: SIMPLE for mu < --simple-mu")
+    p.add_argument("--simple-mu", type=float, default=None, help="hybrid switch (default 1e-5)")
     a = p.parse_args(argv)
 
     from ot_inputs import config_densities
 
     n, K, r0, r1 = config_densities(a.workload, a.n) if a.workload == "mixN" else config_densities(a.workload)
+    if a.K is not None:
+        K = a.K
     mesh = capi.Mesh(n)
     r0d = torch.from_numpy(r0).cuda()
     r1d = torch.from_numpy(r1).cuda()
@@ -56,6 +62,10 @@ def main(argv=None):
         extra["gs_shadow"] = a.gs_shadow
     if a.max_newton is not None:
         extra["max_newton"] = a.max_newton
+    if a.precond is not None:
+        extra["precond"] = a.precond
+    if a.simple_mu is not None:
+        extra["simple_mu"] = a.simple_mu
     opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
     walls, res = [], None
     for _ in range(a.repeat):
@@ -78,6 +88,9 @@ def main(argv=None):
         "gap": st["gap"], "wall_s": walls, "kernel_launches": capi.ot_kernel_launches(),
         "fgmres_restart": opt.fgmres_restart, "fgmres_max_iter": opt.fgmres_max_iter,
         "mu_factor": opt.mu_factor, "mu_final": st["mu"], "graphs": opt.graphs, "gs_shadow": opt.gs_shadow,
+        "precond": ["bb", "simple", "hybrid"][opt.precond], "simple_mu": opt.simple_mu,
+        "stage_newton": st["stage_newton"], "stage_outer": st["stage_outer"], "stage_inner": st["stage_inner"],
+        "stage_seconds": st["stage_seconds"],
     }))
 
 

@@ -114,6 +114,13 @@ def test_solver_entry_points_check_arguments_before_allocating(lib_path):
     assert b"NULL" in lib.ot_last_error()
     bad = capi.default_options(tau=1.5)
     assert lib.ot_ipm_solve(m.handle, p, p, 4, 1.0, 1e-6, ctypes.byref(bad), 0, p, p, p, None, None, None) == 1
+    # the preconditioner choice: BB by default, SIMPLE after mu < 1e-5 in the hybrid; others rejected
+    assert o.precond == capi.OT_PRECOND_BB and abs(o.simple_mu - 1e-5) < 1e-20
+    for bad in (capi.default_options(precond=3), capi.default_options(precond="hybrid", simple_mu=-1.0)):
+        assert lib.ot_ipm_solve(m.handle, p, p, 4, 1.0, 1e-6, ctypes.byref(bad), 0, p, p, p, None, None, None) == 1
+        assert b"precond" in lib.ot_last_error() or b"simple_mu" in lib.ot_last_error()
+    assert lib.ot_simple_apply(m.handle, 4, ctypes.byref(o), p, p, p, p, p, None, p, None) == 1
+    assert b"NULL" in lib.ot_last_error()
 
 
 def test_autotuner_checks_arguments_and_candidates_before_device_work(lib_path):
