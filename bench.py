@@ -88,6 +88,7 @@ def parse_args():
     p.add_argument("--batched-streams", type=int, default=16)
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-stress", action="store_true", help="skip the 256x256, K=64 roofline leg")
+    p.add_argument("--no-grad", action="store_true", help="skip the 128x128, K=32 differentiation leg")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner run")
     return p.parse_args()
 
@@ -403,6 +404,31 @@ def run_ours(args, world, rank, local):
                              for g in sorted(sprof, key=lambda g: -sprof[g][0]) if sprof[g][1] > 0}}
         del smesh
 
+    # the differentiation workload (128x128 squares, K = 32): a full solve to gap 1e-6, then the cost
+    # gradient in rho_in and rho_f by one adjoint solve with the same preconditioner
+    grad = None
+    if not args.no_grad and rank == 0:
+        gn, gK, g0, g1 = config_densities("mix128")
+        gmesh = capi.Mesh(gn)
+        g0d, g1d = torch.from_numpy(g0).to(dev), torch.from_numpy(g1).to(dev)
+        go = capi.default_options(precision=args.precision)
+        capi.ot_ipm_solve(gmesh, g0d, g1d, gK, options=go)  # workspace and graphs set up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gres = capi.ot_ipm_solve(gmesh, g0d, g1d, gK, options=go)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        gin, gf = capi.ot_cost_grad(gmesh, gK, gres["stats"]["mu"], gres["phi"], gres["rho"], gres["s"], g0d, g1d,
+                                    options=go)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        grad = {"workload": "128x128 squares, K=32, 3-Gaussian mixtures (seeds 4/5), floor 1e-4, gap 1e-6",
+                "solve_seconds": t1 - t0, "grad_seconds": t2 - t1,
+                "newton_steps": gres["stats"]["newton_steps"], "fgmres_iters": gres["stats"]["fgmres_iters"],
+                "cost": gres["cost"], "grad_norms": [float(torch.linalg.norm(gin)), float(torch.linalg.norm(gf))],
+                "grad_area_gauge_sums": [float(gin.sum()), float(gf.sum())]}
+        del gmesh
+
     # the autotuner at the final (smallest-mu) state of the solve, where most Newton steps are spent,
     # then one full solve with the settings it picks (reported beside the default settings' time)
     tuned = None
@@ -479,6 +505,7 @@ def run_ours(args, world, rank, local):
         "roofline": roofline,
         "roofline_groups": roofline_groups,
         "stress256": stress,
+        "differentiation": grad,
         "tuned": tuned,
         "kernel_share_ms_per_solve": {k: v[0] for k, v in prof_all.items()},
         "cpu_baseline": cpu,
