@@ -36,7 +36,30 @@ static constexpr int kDotBlocks = 608;  // 4 per SM, each walks one contiguous c
 static constexpr int kUpdBlocks = 608;  // 4 per SM
 static constexpr int kThreads = 256;
 
-size_t kry_partial_doubles(int mmax) { return (size_t)kDotBlocks * (size_t)(mmax + 2) + kUpdBlocks + 64; }
+// Layout of the scratch: per-block dot partials [kDotBlocks][mmax+2], then the
+// update blocks' |w|^2 shares [kUpdBlocks], 64 spare, then 64 doubles holding
+// the arrival counter of the update's last-block reduction (zeroed at
+// allocation; each launch's last block resets it).
+size_t kry_partial_doubles(int mmax) { return (size_t)kDotBlocks * (size_t)(mmax + 2) + kUpdBlocks + 128; }
+size_t kry_counter_offset(int mmax) { return (size_t)kDotBlocks * (size_t)(mmax + 2) + kUpdBlocks + 64; }
+static unsigned* upd_counter(double* partial, int mmax) {
+  return reinterpret_cast<unsigned*>(partial + kry_counter_offset(mmax));
+}
+
+// True in the block that finishes last: every block publishes its global writes
+// (fence), then counts itself in; the block that brings the count to gridDim.x
+// sees every other block's partials and may reduce them (in a fixed order, so
+// the result does not depend on which block came last).  That block resets the
+// counter for the next launch.
+__device__ __forceinline__ bool last_block_done(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
 
 template <typename T>
 __device__ __forceinline__ T kwarp_sum_t(T v) {
@@ -139,7 +162,9 @@ __global__ void __launch_bounds__(kThreads) k_kry_dot_kernel(const T* __restrict
   }
 }
 
-// out[v] = sum over blocks of partial[b * pstride + v], v < nv: one warp per v, fixed order.
+// out[v] = sum over blocks of partial[b * pstride + v], v < nv: one warp per v,
+// fixed order, spread over many blocks (a single last block would walk the
+// nv x blocks partials alone, which costs more than this launch).
 __global__ void k_kry_dot_finish_kernel(const double* __restrict__ partial, int nb, int pstride,
                                         const kry::Ctl* __restrict__ ctl, int add, double* __restrict__ out) {
   const int nv = ctl->j + add;
@@ -166,9 +191,58 @@ void kry_dot(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const T
   prof::end(prof::MDOT, s, nv_hint >= 0 ? (double)sizeof(T) * (nv_hint + 1.0) * (double)n : 0.0);
 }
 
+// ------------------------------------------------------------------ Givens step
+// Column j of H: the two passes' coefficients, the norm after the second pass
+// below the diagonal; the earlier rotations, then the one that zeroes H(j+1, j);
+// the residual estimate, the status, j += 1 and the loop condition.  One thread.
+__device__ void givens_step(const KryGivens& a) {
+  kry::Ctl* c = a.ctl;
+  const double* hc1 = a.hc1;
+  const double* hc2 = a.hc2;
+  const int j = c->j;
+  double* col = a.H + (i64)j * a.ldh;
+  const double hn = sqrt(fmax(hc2[j + 1], 0.0));
+  double carry = (hc1 ? hc1[0] : 0.0) + hc2[0];
+  for (int i = 0; i < j; ++i) {
+    const double x = carry, y = (hc1 ? hc1[i + 1] : 0.0) + hc2[i + 1];
+    col[i] = a.cs[i] * x + a.sn[i] * y;
+    carry = -a.sn[i] * x + a.cs[i] * y;
+  }
+  const double x = carry, y = hn;
+  const double den = hypot(x, y);
+  const double cj = den > 0 ? x / den : 1.0, sj = den > 0 ? y / den : 0.0;
+  a.cs[j] = cj;
+  a.sn[j] = sj;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  const double gj = a.g[j];
+  a.g[j + 1] = -sj * gj;
+  a.g[j] = cj * gj;
+  const double r = fabs(a.g[j + 1]);
+  c->res = r;
+  c->j = j + 1;
+  c->total += 1;
+  int st;
+  if (!isfinite(r))
+    st = kry::NONFINITE;
+  else if (r <= c->tol)
+    st = kry::CONVERGED;
+  else if (hn <= 1e-14 * c->beta)
+    st = kry::BREAKDOWN;
+  else if (j + 1 >= c->m || c->base + j + 1 >= c->cap)
+    st = kry::LIMIT;
+  else
+    st = kry::RUNNING;
+  c->status = st;
+  if (a.on) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h, st == kry::RUNNING ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------ update
-// Block share of |w|^2 into partial[block] (after the block's rows are done).
-__device__ __forceinline__ void block_norm_partial(double acc, double* partial) {
+// Block share of |w|^2 into partial[block] (after the block's rows are done);
+// the last block then writes out[nv] = the sum of the shares (fixed order) and,
+// when gv.ctl is set, takes the Givens step that consumes it.
+__device__ __forceinline__ void block_norm_finish(double acc, double* partial, unsigned* counter, int nv,
+                                                  double* out, const KryGivens& gv) {
   __shared__ double sm[kThreads / 32];
   const double a = kwarp_sum(acc);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
@@ -178,16 +252,31 @@ __device__ __forceinline__ void block_norm_partial(double acc, double* partial) 
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q];
     partial[blockIdx.x] = t;
   }
+  if (!last_block_done(counter)) return;
+  double t = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) t += __ldcg(partial + q);
+  t = kwarp_sum(t);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += sm[q];
+    out[nv] = tot;
+    if (gv.ctl) givens_step(gv);
+    *counter = 0u;
+  }
 }
 
 // w -= sum_{v < nv} h[v] V_v over the block's rows, in T; w32 (nullable) =
 // float(new w); partial[block] = this block's share of |new w|^2 when norm is set.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_kry_update_kernel(const T* __restrict__ V, i64 ld,
-                                                                const kry::Ctl* __restrict__ ctl, int add,
+                                                                const kry::Ctl* ctl, int add,
                                                                 const double* __restrict__ h, T* w, i64 n,
-                                                                bool vec, float* w32, bool norm,
-                                                                double* __restrict__ partial) {
+                                                                bool vec, float* w32, double* norm_out,
+                                                                double* __restrict__ partial, unsigned* counter,
+                                                                KryGivens gv) {
   extern __shared__ __align__(16) unsigned char kry_smem[];
   T* hs = reinterpret_cast<T*>(kry_smem);
   typedef Vec16<T> VT;
@@ -237,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_kry_update_kernel(const T* __restr
     if (w32) w32[i] = (float)wi;
     acc += wi * wi;
   }
-  if (norm) block_norm_partial((double)acc, partial);
+  if (norm_out) block_norm_finish((double)acc, partial, counter, nv, norm_out, gv);
 }
 
 // The same update applied to an FP64 w from the FP32 copy of the basis, the
@@ -246,10 +335,11 @@ __global__ void __launch_bounds__(kThreads) k_kry_update_kernel(const T* __restr
 // correction is ~1e-14 of |w| (FP64 level).  Reads 4 bytes per basis entry
 // instead of 8 and keeps the FP64 units out of the loop.
 __global__ void __launch_bounds__(kThreads) k_kry_update_shadow_kernel(const float* __restrict__ V, i64 ld,
-                                                                       const kry::Ctl* __restrict__ ctl, int add,
+                                                                       const kry::Ctl* ctl, int add,
                                                                        const double* __restrict__ h, double* w,
-                                                                       i64 n, bool vec, bool norm,
-                                                                       double* __restrict__ partial) {
+                                                                       i64 n, bool vec, double* norm_out,
+                                                                       double* __restrict__ partial,
+                                                                       unsigned* counter, KryGivens gv) {
   extern __shared__ __align__(16) unsigned char kry_smem[];
   float* hs = reinterpret_cast<float*>(kry_smem);
   const int nv = ctl->j + add;
@@ -301,74 +391,67 @@ __global__ void __launch_bounds__(kThreads) k_kry_update_shadow_kernel(const flo
     w[i] = wi;
     acc += wi * wi;
   }
-  if (norm) block_norm_partial(acc, partial);
+  if (norm_out) block_norm_finish(acc, partial, counter, nv, norm_out, gv);
 }
 
-// out[nv] = sum of the blocks' |w|^2 shares (one block, fixed order).
-__global__ void k_kry_norm_finish_kernel(const double* __restrict__ partial, int nb, const kry::Ctl* __restrict__ ctl,
-                                         int add, double* __restrict__ out) {
-  __shared__ double sm[32];
-  double t = 0.0;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) t += partial[q];
-  t = kwarp_sum(t);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sm[q];
-    out[ctl->j + add] = a;
-  }
+
+static KryGivens no_givens() {
+  KryGivens g;
+  g.ctl = nullptr;
+  return g;
 }
 
 template <typename T>
 void kry_update(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, T* w, i64 n,
-                float* w32, double* norm_out, double* partial, int nv_hint, Stream s) {
+                float* w32, double* norm_out, double* partial, int nv_hint, Stream s, const KryGivens* gv) {
   prof::begin(prof::MUPDATE, s);
   const size_t smem = sizeof(T) * (size_t)(mmax + 2);
   const bool vec = aligned16(V, w, ld, sizeof(T));
   double* np = partial + (size_t)kDotBlocks * (size_t)(mmax + 2);
-  launch(k_kry_update_kernel<T>, kUpdBlocks, kThreads, smem, cs(s), V, ld, ctl, add, h, w, n, vec, w32,
-         norm_out != nullptr, np);
-  if (norm_out) launch(k_kry_norm_finish_kernel, 1, kThreads, 0, cs(s), (const double*)np, kUpdBlocks, ctl, add, norm_out);
+  launch(k_kry_update_kernel<T>, kUpdBlocks, kThreads, smem, cs(s), V, ld, ctl, add, h, w, n, vec, w32, norm_out,
+         np, upd_counter(partial, mmax), (norm_out && gv) ? *gv : no_givens());
   // the nv basis vectors and w read, w (and its FP32 copy) written
   prof::end(prof::MUPDATE, s,
             nv_hint >= 0 ? (double)sizeof(T) * (nv_hint + 2.0) * (double)n + (w32 ? 4.0 * (double)n : 0.0) : 0.0);
 }
 
 void kry_update_shadow(const float* V32, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, double* w,
-                       i64 n, double* norm_out, double* partial, int nv_hint, Stream s) {
+                       i64 n, double* norm_out, double* partial, int nv_hint, Stream s, const KryGivens* gv) {
   prof::begin(prof::MUPDATE, s);
   const size_t smem = sizeof(float) * (size_t)(mmax + 2);
   const bool vec = aligned16(V32, w, ld, sizeof(float)) && ((uintptr_t)w % 32) == 0;
   double* np = partial + (size_t)kDotBlocks * (size_t)(mmax + 2);
-  launch(k_kry_update_shadow_kernel, kUpdBlocks, kThreads, smem, cs(s), V32, ld, ctl, add, h, w, n, vec,
-         norm_out != nullptr, np);
-  if (norm_out) launch(k_kry_norm_finish_kernel, 1, kThreads, 0, cs(s), (const double*)np, kUpdBlocks, ctl, add, norm_out);
+  launch(k_kry_update_shadow_kernel, kUpdBlocks, kThreads, smem, cs(s), V32, ld, ctl, add, h, w, n, vec, norm_out,
+         np, upd_counter(partial, mmax), (norm_out && gv) ? *gv : no_givens());
   // the nv FP32 basis vectors read, w read and written
   prof::end(prof::MUPDATE, s, nv_hint >= 0 ? 4.0 * nv_hint * (double)n + 16.0 * (double)n : 0.0);
 }
 
 // ------------------------------------------------------------------ basis vectors
+// With j = ctl->j + add: V_{j+1} = w / sqrt(nrm2[j+1]) (and its FP32 copy and
+// `copy`), and Z_j = zsrc when zsrc is given.
 template <typename T>
 __global__ void k_kry_next_basis_kernel(const T* __restrict__ w, const double* __restrict__ nrm2,
-                                        const kry::Ctl* __restrict__ ctl, T* V, i64 ld, float* V32, T* copy,
-                                        i64 n) {
-  const int j = ctl->j;
+                                        const kry::Ctl* __restrict__ ctl, int add, T* V, i64 ld, float* V32, T* copy,
+                                        const T* __restrict__ zsrc, T* Z, i64 n) {
+  const int j = ctl->j + add;
   const T f = (T)(1.0 / sqrt(nrm2[j + 1]));
   T* dst = V + (i64)(j + 1) * ld;
   float* d32 = V32 ? V32 + (i64)(j + 1) * ld : nullptr;
+  T* zdst = zsrc ? Z + (i64)j * ld : nullptr;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     const T v = w[i] * f;
     dst[i] = v;
     if (d32) d32[i] = (float)v;
     if (copy) copy[i] = v;
+    if (zdst) zdst[i] = zsrc[i];
   }
 }
 
 template <typename T>
-void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, T* V, i64 ld, float* V32, T* copy, i64 n,
-                    Stream s) {
-  launch(k_kry_next_basis_kernel<T>, 1216, kThreads, 0, cs(s), w, nrm2, ctl, V, ld, V32, copy, n);
+void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, int add, T* V, i64 ld, float* V32, T* copy,
+                    const T* zsrc, T* Z, i64 n, Stream s) {
+  launch(k_kry_next_basis_kernel<T>, 1216, kThreads, 0, cs(s), w, nrm2, ctl, add, V, ld, V32, copy, zsrc, Z, n);
 }
 
 template <typename T>
@@ -386,18 +469,6 @@ __global__ void k_kry_start_basis_kernel(const T* __restrict__ r, const double* 
 template <typename T>
 void kry_start_basis(const T* r, const double* nrm2, T* V0, float* V32_0, T* copy, i64 n, Stream s) {
   launch(k_kry_start_basis_kernel<T>, 1216, kThreads, 0, cs(s), r, nrm2, V0, V32_0, copy, n);
-}
-
-template <typename T>
-__global__ void k_kry_to_slot_kernel(const T* __restrict__ src, T* base, i64 ld, const kry::Ctl* __restrict__ ctl,
-                                     int add, i64 n) {
-  T* dst = base + (i64)(ctl->j + add) * ld;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) dst[i] = src[i];
-}
-
-template <typename T>
-void kry_to_slot(const T* src, T* base, i64 ld, const kry::Ctl* ctl, int add, i64 n, Stream s) {
-  launch(k_kry_to_slot_kernel<T>, 1216, kThreads, 0, cs(s), src, base, ld, ctl, add, n);
 }
 
 // ------------------------------------------------------------------ control
@@ -442,56 +513,6 @@ __global__ void k_kry_start_kernel(kry::Ctl* c, const double* nrm2, int m, doubl
 
 void kry_start(kry::Ctl* ctl, const double* nrm2, int m, double tol_rel, double* g, CondHandle h, Stream s) {
   launch(k_kry_start_kernel, 1, 32, 0, cs(s), ctl, nrm2, m, tol_rel, g, h.h, (int)h.on);
-}
-
-// Column j of H: the two passes' coefficients, the norm after the second pass
-// below the diagonal; the earlier rotations, then the one that zeroes H(j+1, j).
-__global__ void k_kry_givens_kernel(kry::Ctl* __restrict__ c, const double* __restrict__ hc1,
-                                    const double* __restrict__ hc2, double* __restrict__ H, int ldh,
-                                    double* __restrict__ cs_, double* __restrict__ sn, double* __restrict__ g,
-                                    unsigned long long h, int on) {
-  if (threadIdx.x != 0) return;
-  const int j = c->j;
-  double* col = H + (i64)j * ldh;
-  const double hn = sqrt(fmax(hc2[j + 1], 0.0));
-  double carry = (hc1 ? hc1[0] : 0.0) + hc2[0];
-  for (int i = 0; i < j; ++i) {
-    const double a = carry, b = (hc1 ? hc1[i + 1] : 0.0) + hc2[i + 1];
-    col[i] = cs_[i] * a + sn[i] * b;
-    carry = -sn[i] * a + cs_[i] * b;
-  }
-  const double a = carry, b = hn;
-  const double den = hypot(a, b);
-  const double cj = den > 0 ? a / den : 1.0, sj = den > 0 ? b / den : 0.0;
-  cs_[j] = cj;
-  sn[j] = sj;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  const double gj = g[j];
-  g[j + 1] = -sj * gj;
-  g[j] = cj * gj;
-  const double r = fabs(g[j + 1]);
-  c->res = r;
-  c->j = j + 1;
-  c->total += 1;
-  int st;
-  if (!isfinite(r))
-    st = kry::NONFINITE;
-  else if (r <= c->tol)
-    st = kry::CONVERGED;
-  else if (hn <= 1e-14 * c->beta)
-    st = kry::BREAKDOWN;
-  else if (j + 1 >= c->m || c->base + j + 1 >= c->cap)
-    st = kry::LIMIT;
-  else
-    st = kry::RUNNING;
-  c->status = st;
-  if (on) cudaGraphSetConditional((cudaGraphConditionalHandle)h, st == kry::RUNNING ? 1u : 0u);
-}
-
-void kry_givens(kry::Ctl* ctl, const double* hc1, const double* hc2, double* H, int ldh, double* csv, double* sn,
-                double* g, CondHandle h, Stream s) {
-  launch(k_kry_givens_kernel, 1, 32, 0, cs(s), ctl, hc1, hc2, H, ldh, csv, sn, g, h.h, (int)h.on);
 }
 
 // y = R^{-1} g[0..k) by columns (one warp): y_i = g_i / R_ii, then g_r -= R_ri y_i for r < i.
@@ -584,10 +605,10 @@ void kry_combine(const T* Z, i64 ld, const kry::Ctl* ctl, int mmax, const double
   template void kry_dot<T>(const T*, i64, const kry::Ctl*, int, int, const T*, i64, double*, double*, int,     \
                            Stream);                                                                             \
   template void kry_update<T>(const T*, i64, const kry::Ctl*, int, int, const double*, T*, i64, float*,         \
-                              double*, double*, int, Stream);                                                   \
-  template void kry_next_basis<T>(const T*, const double*, const kry::Ctl*, T*, i64, float*, T*, i64, Stream);  \
+                              double*, double*, int, Stream, const KryGivens*);                                 \
+  template void kry_next_basis<T>(const T*, const double*, const kry::Ctl*, int, T*, i64, float*, T*, const T*, \
+                                  T*, i64, Stream);                                                             \
   template void kry_start_basis<T>(const T*, const double*, T*, float*, T*, i64, Stream);                       \
-  template void kry_to_slot<T>(const T*, T*, i64, const kry::Ctl*, int, i64, Stream);                           \
   template void kry_combine<T>(const T*, i64, const kry::Ctl*, int, const double*, T*, i64, int, Stream);
 OT_KRY_INST(double)
 OT_KRY_INST(float)

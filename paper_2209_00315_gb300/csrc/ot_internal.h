@@ -181,42 +181,55 @@ size_t k_reduce_scratch(int nv);  // doubles needed by `partial`
 // ctl->j + add) and their grids depend only on the basis size mmax, so one
 // capture serves every step.  Coefficients and norms are double; T is the
 // basis precision (double, or float for the inner Schur solve).
-size_t kry_partial_doubles(int mmax);  // scratch doubles of kry_dot / kry_update
+size_t kry_partial_doubles(int mmax);  // scratch doubles of kry_dot / kry_update (incl. an arrival counter)
+size_t kry_counter_offset(int mmax);   // first double of the arrival counter inside that scratch
+// The Givens step of an Arnoldi iteration (column j of the Hessenberg matrix
+// from the two Gram-Schmidt passes, hc1 nullable; the earlier rotations and the
+// new one; residual estimate, status, j += 1, loop condition h), taken by the
+// last block of the update that produces |w|^2.
+struct KryGivens {
+  kry::Ctl* ctl;
+  const double* hc1;
+  const double* hc2;
+  double* H;
+  int ldh;
+  double* cs;
+  double* sn;
+  double* g;
+  unsigned long long h;
+  int on;
+};
 // out[v] = <V_v, w>, v < nv.
 // nv_hint: nv when the host knows it (eager loops; kernel-timing bytes only), else -1.
 template <typename T>
 void kry_dot(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const T* w, i64 n, double* out,
              double* partial, int nv_hint, Stream s);
 // w -= sum_{v < nv} h[v] V_v; w32 (nullable) receives the new w in float;
-// norm_out (nullable): norm_out[nv] = |new w|^2.
+// norm_out (nullable): norm_out[nv] = |new w|^2, followed by the Givens step gv
+// (nullable) in the same launch.
 template <typename T>
 void kry_update(const T* V, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, T* w, i64 n,
-                float* w32, double* norm_out, double* partial, int nv_hint, Stream s);
+                float* w32, double* norm_out, double* partial, int nv_hint, Stream s, const KryGivens* gv = nullptr);
 // The same update of an FP64 w from an FP32 basis (the FP32 copy of V), the
 // combination formed in FP32: for the second Gram-Schmidt pass, whose
 // coefficients are ~1e-7 of |w|.
 void kry_update_shadow(const float* V32, i64 ld, const kry::Ctl* ctl, int add, int mmax, const double* h, double* w,
-                       i64 n, double* norm_out, double* partial, int nv_hint, Stream s);
-// V_{j+1} = w / sqrt(nrm2[j+1]), j = ctl->j; V32 (nullable) and copy (nullable) receive it too.
+                       i64 n, double* norm_out, double* partial, int nv_hint, Stream s,
+                       const KryGivens* gv = nullptr);
+// With j = ctl->j + add: V_{j+1} = w / sqrt(nrm2[j+1]); V32 (nullable) and copy
+// (nullable) receive it too; Z_j = zsrc when zsrc is given.
 template <typename T>
-void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, T* V, i64 ld, float* V32, T* copy, i64 n,
-                    Stream s);
+void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, int add, T* V, i64 ld, float* V32, T* copy,
+                    const T* zsrc, T* Z, i64 n, Stream s);
 // V0 = r / sqrt(nrm2[0]); V32_0 (nullable) and copy (nullable) receive it too.
 template <typename T>
 void kry_start_basis(const T* r, const double* nrm2, T* V0, float* V32_0, T* copy, i64 n, Stream s);
-// base[(ctl->j + add) * ld + i] = src[i]
-template <typename T>
-void kry_to_slot(const T* src, T* base, i64 ld, const kry::Ctl* ctl, int add, i64 n, Stream s);
 // Once per linear solve: base = 0, cap, tol = tol_rel * sqrt(sum_{i < nref} ref[i]) (nref > 0).
 void kry_solve_init(kry::Ctl* ctl, const double* ref, int nref, double tol_rel, int cap, Stream s);
 // Start of a cycle: beta = sqrt(nrm2[0]), g[0] = beta, j = 0; with tol_rel > 0 the
 // tolerance becomes tol_rel * beta; status RUNNING unless beta is already small
 // enough (or not finite); the loop condition h (if any) follows the status.
 void kry_start(kry::Ctl* ctl, const double* nrm2, int m, double tol_rel, double* g, CondHandle h, Stream s);
-// Column j of the Hessenberg matrix from the two Gram-Schmidt passes (hc1
-// nullable), Givens rotations, residual estimate, status, j += 1, condition.
-void kry_givens(kry::Ctl* ctl, const double* hc1, const double* hc2, double* H, int ldh, double* cs, double* sn,
-                double* g, CondHandle h, Stream s);
 // y = R^{-1} g over the ctl->j columns (ctl->k = j, ctl->base += j).
 void kry_backsolve(kry::Ctl* ctl, const double* H, int ldh, const double* g, double* y, Stream s);
 // x += sum_{v < ctl->k} y[v] Z_v

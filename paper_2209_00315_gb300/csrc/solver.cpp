@@ -105,6 +105,7 @@ void KrylovT<T>::build(int m, i64 n_, bool shadow) {
   sn = (double*)dev::alloc(sizeof(double) * (m + 1));
   g = (double*)dev::alloc(sizeof(double) * (m + 2));
   part = (double*)dev::alloc(sizeof(double) * kry_partial_doubles(m));
+  dev::zero(part + kry_counter_offset(m), 64 * sizeof(double), nullptr);  // arrival counters
   scal = (double*)dev::alloc(sizeof(double) * 8);
   kry::Ctl c0;
   std::memset(&c0, 0, sizeof(c0));
@@ -354,15 +355,16 @@ template <typename T>
 using OpFn = std::function<void(const T*, T*, Stream)>;
 
 // One Arnoldi step of right-preconditioned (flexible) GMRES, enqueued on st:
-// z_j = M^{-1} v_j (v_j is K.in), z_j stored in Z, w = A z_j, classical
-// Gram-Schmidt with one reorthogonalisation against v_0..v_j (the step count
-// j is read by the kernels from K.ctl), v_{j+1} = w/|w| (also written to
-// K.in), then the Givens kernel updates the least-squares problem and decides
-// whether another step runs.  With an FP32 shadow of the basis (shadow) the
-// dot products of the first pass, and of the second when fp32_reorth is set,
-// are taken from it in FP32; every coefficient is applied to the FP64 basis
-// and H records exactly the coefficients applied, so the Arnoldi relation
-// A Z = V H holds to FP64 rounding whichever precision computed them.
+// z_j = M^{-1} v_j (v_j is K.in), w = A z_j, classical Gram-Schmidt with one
+// reorthogonalisation against v_0..v_j (the step count j is read by the kernels
+// from K.ctl), the last block of the final update sums |w|^2 and takes the
+// Givens step (least squares, status, j += 1, loop condition), then one kernel
+// writes v_{j+1} = w/|w| (also to K.in) and stores z_j in Z: seven or eight
+// launches besides M and A.  With an FP32 shadow of the basis (shadow) the dot
+// products of the first pass, and of the second when fp32_reorth is set, are
+// taken from it in FP32; every coefficient is applied to the FP64 basis and H
+// records exactly the coefficients applied, so the Arnoldi relation A Z = V H
+// holds to FP64 rounding whichever precision computed them.
 // Second-pass coefficients from the shadow limit the orthogonality of V to
 // ~1e-7, which moves the residual estimate by that relative amount: harmless
 // for a target of 1e-5, so fgmres() asks for it only for targets >= 1e-8.  In
@@ -374,8 +376,19 @@ static void arnoldi_step(KrylovT<T>& K, const OpFn<T>& prec, const OpFn<T>& op, 
                          Stream st, CondHandle h, int j) {
   const i64 n = K.n;
   const int nv = j >= 0 ? j + 1 : -1;
+  // the Givens step rides on the last update (its last block, once |w|^2 is summed)
+  KryGivens gv;
+  gv.ctl = K.ctl;
+  gv.hc1 = K.hc1;
+  gv.hc2 = K.hc2;
+  gv.H = K.H;
+  gv.ldh = K.ldh();
+  gv.cs = K.cs;
+  gv.sn = K.sn;
+  gv.g = K.g;
+  gv.h = h.h;
+  gv.on = (int)h.on;
   prec(K.in, K.zout, st);
-  kry_to_slot<T>(K.zout, K.Z, n, K.ctl, 0, n, st);
   op(K.zout, K.w, st);
   if constexpr (std::is_same<T, double>::value) shadow = shadow && K.V32 != nullptr;
   else shadow = false;  // FP32 bases have no shadow
@@ -386,20 +399,21 @@ static void arnoldi_step(KrylovT<T>& K, const OpFn<T>& prec, const OpFn<T>& op, 
       // second pass entirely from the shadow: dots, and the update formed in FP32
       kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc1, K.w, n, K.w32, nullptr, K.part, nv, st);
       kry_dot<float>(K.V32, n, K.ctl, 1, K.mmax, K.w32, n, K.hc2, K.part, nv, st);
-      kry_update_shadow(K.V32, n, K.ctl, 1, K.mmax, K.hc2, reinterpret_cast<double*>(K.w), n, K.hc2, K.part, nv, st);
+      kry_update_shadow(K.V32, n, K.ctl, 1, K.mmax, K.hc2, reinterpret_cast<double*>(K.w), n, K.hc2, K.part, nv, st,
+                        &gv);
     } else {
       kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc1, K.w, n, nullptr, nullptr, K.part, nv, st);
       kry_dot<T>(K.V, n, K.ctl, 1, K.mmax, K.w, n, K.hc2, K.part, nv, st);
-      kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st);
+      kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st, &gv);
     }
   } else {
     kry_dot<T>(K.V, n, K.ctl, 1, K.mmax, K.w, n, K.hc1, K.part, nv, st);
     kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc1, K.w, n, nullptr, nullptr, K.part, nv, st);
     kry_dot<T>(K.V, n, K.ctl, 1, K.mmax, K.w, n, K.hc2, K.part, nv, st);
-    kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st);
+    kry_update<T>(K.V, n, K.ctl, 1, K.mmax, K.hc2, K.w, n, nullptr, K.hc2, K.part, nv, st, &gv);
   }
-  kry_next_basis<T>(K.w, K.hc2, K.ctl, K.V, n, shadow ? K.V32 : nullptr, K.in, n, st);
-  kry_givens(K.ctl, K.hc1, K.hc2, K.H, K.ldh(), K.cs, K.sn, K.g, h, st);
+  // the Givens step advanced ctl->j: the new basis vector and the Z slot of this step are j - 1 + 1 and j - 1
+  kry_next_basis<T>(K.w, K.hc2, K.ctl, -1, K.V, n, shadow ? K.V32 : nullptr, K.in, K.zout, K.Z, n, st);
 }
 
 // One (F)GMRES cycle on stream st: start vector r (in K.w on entry of the
