@@ -39,6 +39,9 @@ def main(argv=None):
     p.add_argument("--precond", choices=["bb", "simple", "hybrid"], default=None,
                    help="outer preconditioner (default bb); hybrid: SIMPLE for mu < --simple-mu")
     p.add_argument("--simple-mu", type=float, default=None, help="hybrid switch (default 1e-5)")
+    p.add_argument("--smooth-sweeps", type=int, default=None, help="multigrid pre/post sweeps per level")
+    p.add_argument("--coarse-sweeps", type=int, default=None, help="multigrid sweeps on the coarsest level")
+    p.add_argument("--lap-cycles", type=int, default=None, help="V-cycles per slice-Laplacian solve")
     a = p.parse_args(argv)
 
     from ot_inputs import config_densities
@@ -66,6 +69,9 @@ def main(argv=None):
         extra["precond"] = a.precond
     if a.simple_mu is not None:
         extra["simple_mu"] = a.simple_mu
+    for f in ("smooth_sweeps", "coarse_sweeps", "lap_cycles"):
+        if getattr(a, f) is not None:
+            extra[f] = getattr(a, f)
     opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
     walls, res = [], None
     for _ in range(a.repeat):
@@ -89,6 +95,7 @@ def main(argv=None):
         "fgmres_restart": opt.fgmres_restart, "fgmres_max_iter": opt.fgmres_max_iter,
         "mu_factor": opt.mu_factor, "mu_final": st["mu"], "graphs": opt.graphs, "gs_shadow": opt.gs_shadow,
         "precond": ["bb", "simple", "hybrid"][opt.precond], "simple_mu": opt.simple_mu,
+        "smooth_sweeps": opt.smooth_sweeps, "coarse_sweeps": opt.coarse_sweeps, "lap_cycles": opt.lap_cycles,
         "stage_newton": st["stage_newton"], "stage_outer": st["stage_outer"], "stage_inner": st["stage_inner"],
         "stage_seconds": st["stage_seconds"],
     }))
