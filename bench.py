@@ -365,11 +365,13 @@ def run_ours(args, world, rank, local):
     peak_source = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
 
     def group_roofline(prof, name, workload=WORKLOAD):
+        # groups whose byte count lives on the device (the Krylov combine's vector count) report None
         t_ms, t_n, t_b = prof[name]
-        achieved = (t_b / 1e9) / (t_ms / 1e3) if t_ms > 0 else 0.0
+        achieved = (t_b / 1e9) / (t_ms / 1e3) if t_ms > 0 and t_b > 0 else None
         alg = t_b / max(t_n, 1)
         return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": group_traffic(workload, name, alg), "launches": t_n,
+                "frac": achieved / peak if achieved is not None else None,
+                "traffic": group_traffic(workload, name, alg), "launches": t_n,
                 "avg_launch_us": 1e3 * t_ms / max(t_n, 1), "algorithmic_bytes_per_launch": alg,
                 "peak_source": peak_source}
 
