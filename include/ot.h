@@ -108,6 +108,9 @@ typedef struct {
                                solved by GMRES to eps_schur (at most schur_max_iter iterations),
                                preconditioned by exact solves of its time-line (tridiagonal) part */
   double simple_mu;         /* HYBRID: SIMPLE for the stages with mu < simple_mu (1e-5) */
+  int32_t pdl;              /* 1 (default): the solver's kernels use programmatic dependent launch (each
+                               may be scheduled while its predecessor's last blocks finish, then waits
+                               for its results); 0: plain stream order.  Results are the same */
 } ot_options;
 
 #define OT_MAX_STAGES 40

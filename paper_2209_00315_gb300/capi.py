@@ -50,7 +50,8 @@ class ot_options(C.Structure):
                 ("fgmres_restart", C.c_int32), ("fgmres_max_iter", C.c_int32), ("schur_max_iter", C.c_int32),
                 ("lap_cycles", C.c_int32), ("smooth_sweeps", C.c_int32), ("coarse_sweeps", C.c_int32),
                 ("max_newton", C.c_int32), ("verbose", C.c_int32), ("gs_shadow", C.c_int32),
-                ("graphs", C.c_int32), ("precond", C.c_int32), ("simple_mu", C.c_double)]
+                ("graphs", C.c_int32), ("precond", C.c_int32), ("simple_mu", C.c_double),
+                ("pdl", C.c_int32)]
 
 
 class ot_stats(C.Structure):

@@ -77,6 +77,7 @@ void ot_default_options(ot_options* o) {
   o->graphs = 1;
   o->precond = OT_PRECOND_BB;
   o->simple_mu = 1e-5;
+  o->pdl = 1;
 }
 
 const char* ot_last_error(void) { return g_err.c_str(); }
@@ -111,6 +112,7 @@ static ot_options resolve(const ot_options* o) {
   require(r.precond == OT_PRECOND_BB || r.precond == OT_PRECOND_SIMPLE || r.precond == OT_PRECOND_HYBRID,
           "options.precond must be OT_PRECOND_BB, OT_PRECOND_SIMPLE or OT_PRECOND_HYBRID");
   require(r.simple_mu >= 0 && std::isfinite(r.simple_mu), "options.simple_mu must be finite and >= 0");
+  require(r.pdl == 0 || r.pdl == 1, "options.pdl must be 0 or 1");
   return r;
 }
 

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_kry_dot_kernel(const T* __restrict
                                                              const kry::Ctl* __restrict__ ctl, int add,
                                                              const T* __restrict__ w, i64 n, bool vec,
                                                              double* __restrict__ partial, int pstride) {
+  OT_GRID_DEP_WAIT();
   typedef Vec16<T> VT;
   typedef typename VT::type V4;
   constexpr int E = VT::E;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_kry_dot_kernel(const T* __restrict
 // nv x blocks partials alone, which costs more than this launch).
 __global__ void k_kry_dot_finish_kernel(const double* __restrict__ partial, int nb, int pstride,
                                         const kry::Ctl* __restrict__ ctl, int add, double* __restrict__ out) {
+  OT_GRID_DEP_WAIT();
   const int nv = ctl->j + add;
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -277,6 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_kry_update_kernel(const T* __restr
                                                                 bool vec, float* w32, double* norm_out,
                                                                 double* __restrict__ partial, unsigned* counter,
                                                                 KryGivens gv) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char kry_smem[];
   T* hs = reinterpret_cast<T*>(kry_smem);
   typedef Vec16<T> VT;
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_kry_update_shadow_kernel(const flo
                                                                        i64 n, bool vec, double* norm_out,
                                                                        double* __restrict__ partial,
                                                                        unsigned* counter, KryGivens gv) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char kry_smem[];
   float* hs = reinterpret_cast<float*>(kry_smem);
   const int nv = ctl->j + add;
@@ -434,6 +438,7 @@ template <typename T>
 __global__ void k_kry_next_basis_kernel(const T* __restrict__ w, const double* __restrict__ nrm2,
                                         const kry::Ctl* __restrict__ ctl, int add, T* V, i64 ld, float* V32, T* copy,
                                         const T* __restrict__ zsrc, T* Z, i64 n) {
+  OT_GRID_DEP_WAIT();
   const int j = ctl->j + add;
   const T f = (T)(1.0 / sqrt(nrm2[j + 1]));
   T* dst = V + (i64)(j + 1) * ld;
@@ -457,6 +462,7 @@ void kry_next_basis(const T* w, const double* nrm2, const kry::Ctl* ctl, int add
 template <typename T>
 __global__ void k_kry_start_basis_kernel(const T* __restrict__ r, const double* __restrict__ nrm2, T* V0, float* V32,
                                          T* copy, i64 n) {
+  OT_GRID_DEP_WAIT();
   const T f = (T)(1.0 / sqrt(nrm2[0]));
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     const T v = r[i] * f;
@@ -473,6 +479,7 @@ void kry_start_basis(const T* r, const double* nrm2, T* V0, float* V32_0, T* cop
 
 // ------------------------------------------------------------------ control
 __global__ void k_kry_solve_init_kernel(kry::Ctl* c, const double* ref, int nref, double tol_rel, int cap) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0) return;
   c->base = 0;
   c->cap = cap;
@@ -489,6 +496,7 @@ void kry_solve_init(kry::Ctl* ctl, const double* ref, int nref, double tol_rel, 
 
 __global__ void k_kry_start_kernel(kry::Ctl* c, const double* nrm2, int m, double tol_rel, double* g,
                                    unsigned long long h, int on) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0) return;
   const double beta = sqrt(fmax(nrm2[0], 0.0));
   c->beta = beta;
@@ -518,6 +526,7 @@ void kry_start(kry::Ctl* ctl, const double* nrm2, int m, double tol_rel, double*
 // y = R^{-1} g[0..k) by columns (one warp): y_i = g_i / R_ii, then g_r -= R_ri y_i for r < i.
 __global__ void k_kry_backsolve_kernel(kry::Ctl* __restrict__ c, const double* __restrict__ H, int ldh,
                                        const double* __restrict__ g, double* __restrict__ y) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ double gsm[];
   const int k = c->j;
   const int lane = threadIdx.x;
@@ -547,6 +556,7 @@ __global__ void __launch_bounds__(kThreads) k_kry_combine_kernel(const T* __rest
                                                                  const kry::Ctl* __restrict__ ctl,
                                                                  const double* __restrict__ y, T* x, i64 n,
                                                                  bool pairs) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char kry_smem[];
   T* ys = reinterpret_cast<T*>(kry_smem);
   const int nv = ctl->k;

@@ -103,6 +103,7 @@ namespace dev {
 // Threads that drive their own stream allocate stream-ordered from the
 // device's memory pool: no device-wide synchronisation on free, and freed
 // blocks are reused by the next workspace.
+thread_local bool pdl = false;
 static thread_local cudaStream_t t_alloc_stream = nullptr;
 void set_alloc_stream(Stream s) { t_alloc_stream = cs(s); }
 static thread_local size_t t_krylov_budget = (size_t)64 << 30;
@@ -237,6 +238,7 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
 
 // out[v] = sum_b partial[b * stride + v], v < nv (one block per v)
 __global__ void k_finish_sum(const double* partial, int nblocks, int stride, int nv, double* out) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   int v = blockIdx.x;
   if (v >= nv) return;
@@ -249,6 +251,7 @@ __global__ void k_finish_sum(const double* partial, int nblocks, int stride, int
 // ------------------------------------------------------------------ slice sums
 template <typename T>
 __global__ void k_slice_sums_kernel(const T* x, i64 n, double scale, T* sums) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   const T* xs = x + (i64)blockIdx.x * n;
   double a = strided_sum(xs, n);
@@ -262,6 +265,7 @@ void k_slice_sums(const double* x, int S, i64 n, double scale, double* sums, Str
 
 template <typename T>
 __global__ void k_slice_shift_kernel(T* x, int S, i64 n, const T* sums, double scale) {
+  OT_GRID_DEP_WAIT();
   i64 tot = (i64)S * n;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < tot; i += (i64)gridDim.x * blockDim.x)
     x[i] -= (T)(scale * (double)sums[i / n]);
@@ -279,6 +283,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_mdot8_kernel(const T* __restrict__ V, i64 ld, int nv,
                                                       const T* __restrict__ w, i64 n, bool pairs,
                                                       double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[8][8];
   const int v0 = blockIdx.y * 8;
   const int cnt = min(8, nv - v0);
@@ -346,6 +351,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_update_kernel(const T* __restrict__ V, i64 ld, int nv,
                                                        const double* __restrict__ h, T* w, i64 n, bool pairs,
                                                        bool norm, double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ T hs[64];
   __shared__ double sm[32];
   for (int v = threadIdx.x; v < 64; v += blockDim.x) hs[v] = (v < nv) ? (T)h[v] : (T)0;
@@ -411,6 +417,7 @@ void k_mupdate(const double* V, i64 ld, int nv, const double* h, double* w, i64 
 template <typename T>
 __global__ void k_mcombine_kernel(const T* __restrict__ Z, i64 ld, int nv, const double* __restrict__ y, T* x,
                                   i64 n) {
+  OT_GRID_DEP_WAIT();
   __shared__ T ys[64];
   for (int v = threadIdx.x; v < nv && v < 64; v += blockDim.x) ys[v] = (T)y[v];
   __syncthreads();
@@ -436,6 +443,7 @@ void k_mcombine(const double* Z, i64 ld, int nv, const double* y, double* x, i64
 
 template <typename T>
 __global__ void k_dot_kernel(const T* x, const T* y, i64 n, double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   T t = 0;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
@@ -450,6 +458,7 @@ void k_dot(const double* x, const double* y, i64 n, double* out, double* partial
 }
 
 __global__ void k_axpby_kernel(double a, const double* x, double b, double* y, i64 n) {
+  OT_GRID_DEP_WAIT();
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
@@ -459,6 +468,7 @@ void k_axpby(double a, const double* x, double b, double* y, i64 n, Stream s) {
 
 template <typename T>
 __global__ void k_scale_inv_norm_kernel(const T* x, const double* nrm2, T* y, i64 n) {
+  OT_GRID_DEP_WAIT();
   T f = (T)(1.0 / sqrt(nrm2[0]));
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = x[i] * f;
@@ -469,6 +479,7 @@ void k_scale_by_inv_norm(const double* x, const double* nrm2, double* y, i64 n, 
 
 template <typename T>
 __global__ void k_scale_kernel(const T* x, T a, T* y, i64 n) {
+  OT_GRID_DEP_WAIT();
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = a * x[i];
 }
@@ -476,6 +487,7 @@ void k_scale(const double* x, double a, double* y, i64 n, Stream s) {
   launch(k_scale_kernel<double>, blocks_for(n, kThreads, 4096), kThreads, 0, cs(s), x, a, y, n);
 }
 __global__ void k_fill_kernel(double* x, double v, i64 n) {
+  OT_GRID_DEP_WAIT();
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) x[i] = v;
 }
 void k_fill(double* x, double v, i64 n, Stream s) {
@@ -484,6 +496,7 @@ void k_fill(double* x, double v, i64 n, Stream s) {
 
 // ------------------------------------------------------------------ max |x|, min x
 __global__ void k_absmax_kernel(const double* x, i64 n, double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   __shared__ double sb[32];
   double a = 0.0, bad = 0.0;
@@ -506,6 +519,7 @@ __global__ void k_absmax_kernel(const double* x, i64 n, double* partial) {
   }
 }
 __global__ void k_absmax_finish(const double* partial, int nb, double* out) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0) return;
   double a = 0.0, bad = 0.0;
   for (int b = 0; b < nb; ++b) { a = fmax(a, partial[2 * b]); bad = fmax(bad, partial[2 * b + 1]); }
@@ -518,6 +532,7 @@ void k_absmax(const double* x, i64 n, double* out, double* partial, Stream s) {
 }
 
 __global__ void k_min_kernel(const double* x, i64 n, double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   double a = INFINITY;
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
@@ -532,6 +547,7 @@ __global__ void k_min_kernel(const double* x, i64 n, double* partial) {
   }
 }
 __global__ void k_min_finish(const double* partial, int nb, double* out) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0) return;
   double a = INFINITY;
   for (int b = 0; b < nb; ++b) a = fmin(a, partial[b]);

@@ -33,6 +33,7 @@ static inline int nblk(i64 n) {
 // ------------------------------------------------------------------ level-0 coefficients
 template <typename T>
 __global__ void k_lap_coef0_kernel(Dims d, const double* rho, const double* r0, const double* r1, T* alpha) {
+  OT_GRID_DEP_WAIT();
   int S = d.K + 1;
   SLICE_LOOP(jj, S, c, d.N) {
 #pragma unroll
@@ -48,6 +49,7 @@ void k_mg_lap_coef0(const Dims& d, const double* rho, const double* r0, const do
 template <typename T>
 __global__ void k_schur_coef0_kernel(Dims d, const double* phi, const double* rho, const double* s, T* alpha,
                                      T* tau) {
+  OT_GRID_DEP_WAIT();
   int S = d.K;
   SLICE_LOOP(k0, S, C, d.Nc) {
     i64 i = (i64)k0 * d.Nc + C;
@@ -67,6 +69,7 @@ void k_mg_schur_coef0(const Dims& d, const double* phi, const double* rho, const
 // ------------------------------------------------------------------ coarse coefficients
 template <typename T>
 __global__ void k_restrict_coef_kernel(int S, LevelView<T> f, LevelView<T> c) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k, S, C, c.nc) {
     i64 i = (i64)k * c.ld + C;
 #pragma unroll
@@ -93,6 +96,7 @@ void k_mg_restrict_coef(int S, const LevelView<T>& fine, const LevelView<T>& coa
 // ------------------------------------------------------------------ smoothers
 template <typename T>
 __global__ void k_point_smooth_kernel(int S, LevelView<T> L, int color) {
+  OT_GRID_DEP_WAIT();
   i64 sq = (i64)L.m * L.m;
   SLICE_LOOP(k, S, i, sq) point_gs(S, L, k, (i64)color * sq + i);
 }
@@ -104,6 +108,7 @@ __global__ void k_point_smooth_mode_kernel(int S, LevelView<T> L, LevelView<T> L
 
 template <typename T>
 __global__ void k_line_smooth_kernel(int S, LevelView<T> L, int color, T* lc, T* lr) {
+  OT_GRID_DEP_WAIT();
   i64 sq = (i64)L.m * L.m;
   GRID_LOOP(i, sq) line_gs(S, L, (i64)color * sq + i, lc, lr);
 }
@@ -366,6 +371,7 @@ __device__ __forceinline__ int parent_cell(int m, int t, int I, int J) {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_point_rows_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  OT_GRID_DEP_WAIT();
   const int m = L.m, mm = m * m, ld = (int)L.ld;
   const int J = blockIdx.x * 8 + threadIdx.y;
   if (J >= m) return;
@@ -416,6 +422,7 @@ static void launch_point_rows(int S, const LevelView<T>& L, const LevelView<T>& 
 
 template <typename T, int KPL>
 __global__ void __launch_bounds__(256) k_line_pcr_kernel(int S, LevelView<T> L, int color) {
+  OT_GRID_DEP_WAIT();
   i64 sq = (i64)L.m * L.m;
   int lane = threadIdx.x & 31;
   i64 w0 = (blockIdx.x * (i64)blockDim.x + threadIdx.x) >> 5;
@@ -530,6 +537,7 @@ __device__ __forceinline__ void tile_store(int S, const LevelView<T>& L, int col
 
 template <typename T, int TC, int KPL, int MODE>
 __global__ void __launch_bounds__(32 * TC) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tsm = reinterpret_cast<T*>(smem_raw);
   tile_gather<T, TC, KPL, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
@@ -542,6 +550,7 @@ __global__ void __launch_bounds__(32 * TC) k_line_pcr_tile_kernel(int S, LevelVi
 // Thomas factors of every line of a level in device memory (once per Newton step).
 template <typename T>
 __global__ void k_line_factor_kernel(int S, LevelView<T> L) {
+  OT_GRID_DEP_WAIT();
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)L.nc; c += gridDim.x * blockDim.x) line_factor(S, L, c);
 }
 
@@ -634,6 +643,7 @@ __device__ __forceinline__ void tile_solve_fac(int S, int tid, T* tsm) {
 
 template <typename T, int TC, int KPL, int MODE>
 __global__ void __launch_bounds__(32 * TC) k_line_scan_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tsm = reinterpret_cast<T*>(smem_raw);
   tile_gather_fac<T, TC, KPL, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
@@ -741,6 +751,7 @@ void k_mg_smooth(int S, const LevelView<T>& L, int color, T* line_c, T* line_r, 
 
 template <typename T, int MODE>
 __global__ void k_point_smooth_mode_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
+  OT_GRID_DEP_WAIT();
   const int sq = L.m * L.m;
   SLICE_LOOP(k, S, i, sq) point_gs_mode<T, MODE>(S, L, Lc, k, color * sq + (int)i);
 }
@@ -788,6 +799,7 @@ void k_mg_smooth_mode(int S, const LevelView<T>& L, const LevelView<T>* coarse, 
 // ------------------------------------------------------------------ residual and transfers
 template <typename T>
 __global__ void k_residual_kernel(int S, LevelView<T> L) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k, S, c, L.nc) {
     i64 i = (i64)k * L.ld + c;
     L.r[i] = L.b[i] - level_apply(S, L, k, c);
@@ -803,6 +815,7 @@ void k_mg_residual(int S, const LevelView<T>& L, Stream st) {
 
 template <typename T>
 __global__ void k_restrict_kernel(int S, LevelView<T> f, LevelView<T> c) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k, S, C, c.nc) {
     i64 i = (i64)k * c.ld + C;
     i64 ch[4];
@@ -821,6 +834,7 @@ void k_mg_restrict(int S, const LevelView<T>& fine, const LevelView<T>& coarse, 
 // sums its four children's residuals (same sums, same order as residual + restrict).
 template <typename T>
 __global__ void k_restrict_residual_kernel(int S, LevelView<T> f, LevelView<T> c) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k, S, C, c.nc) {
     i64 ch[4];
     children(c.m, decode(c.m, C), ch);
@@ -858,6 +872,7 @@ __device__ __forceinline__ T level_apply_row(int S, const LevelView<T>& L, int k
 // b_coarse = J^T (b - M x) with a warp per row of coarse squares (as k_restrict_residual_kernel).
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_residual_rows(int S, LevelView<T> f, LevelView<T> c) {
+  OT_GRID_DEP_WAIT();
   const int n = c.m, nn = n * n, m = f.m, mm = m * m, fld = (int)f.ld, cld = (int)c.ld;
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -888,6 +903,7 @@ void k_mg_restrict_residual(int S, const LevelView<T>& fine, const LevelView<T>&
 
 template <typename T>
 __global__ void k_prolong_kernel(int S, LevelView<T> c, LevelView<T> f) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k, S, cf, f.nc) f.x[(i64)k * f.ld + cf] += c.x[(i64)k * c.ld + parent_of(f.m, cf)];
 }
 
@@ -1108,6 +1124,7 @@ __device__ void coarse_body(int S, const LevelView<T>& L, int sweeps, T* lc, T* 
 template <typename T, int KPL>
 __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_coarse_kernel(int S, LevelView<T> L, int sweeps,
                                                                                 T* lc, T* lr, T* agg) {
+  OT_GRID_DEP_WAIT();
   coarse_body<T, KPL>(S, L, sweeps, lc, lr, agg);
 }
 
@@ -1255,6 +1272,7 @@ size_t fused_smem_bytes(const LevelView<T>* lv, int nlev, int S_view, bool tc) {
 constexpr int kLapLowerThreads = 1024;  // one cell per thread and colour phase on a side-32 level
 template <typename T>
 __global__ void __launch_bounds__(kLapLowerThreads) k_lap_lower_kernel(int S, LevelSet<T> gls, int nu, int nuc) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k = blockIdx.x;
   __shared__ LevelSet<T> ls;
@@ -1394,6 +1412,7 @@ __device__ void sch_lower_body(int S, const LevelSet<T>& gls, int nu, int nuc, u
 template <typename T, int KPL>
 __global__ void __launch_bounds__(sch_lower_threads<T, KPL>()) k_sch_lower_kernel(int S, LevelSet<T> gls, int nu,
                                                                                    int nuc) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   sch_lower_body<T, KPL>(S, gls, nu, nuc, smem_raw);
 }
@@ -1462,6 +1481,7 @@ void k_mg_lower_cycle(int S, const LevelView<T>* levels, int nlev, int nu, int n
 // ------------------------------------------------------------------ conversions
 template <typename T>
 __global__ void k_load_kernel(const double* src, double scale, T* b, T* x, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) {
     b[i] = (T)(scale * src[i]);
     if (x) x[i] = 0;
@@ -1474,6 +1494,7 @@ void k_mg_load(const double* src, double scale, T* b, T* x, i64 n, Stream st) {
 
 template <typename T>
 __global__ void k_store_kernel(const T* x, double* dst, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) dst[i] = (double)x[i];
 }
 template <typename T>
@@ -1506,6 +1527,7 @@ OT_INST(double)
 namespace ot {
 template <typename T>
 __global__ void k_axpy_t_kernel(const T* x, T a, T* y, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) y[i] += a * x[i];
 }
 template <typename T>

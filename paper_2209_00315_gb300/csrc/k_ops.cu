@@ -46,6 +46,7 @@ static const dim3 kRowsBlock(32, 8);
 template <typename T>
 __global__ void __launch_bounds__(256) k_schur_u_rows(Dims d, const T* __restrict__ phi, const T* __restrict__ z,
                                                       T* __restrict__ u) {
+  OT_GRID_DEP_WAIT();
   const int m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
   ROWS_SQUARE(m, I, J)
   for (int jj = blockIdx.z; jj < d.K + 1; jj += gridDim.z) {
@@ -78,6 +79,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_schur_out_rows(Dims d, const T* __restrict__ phi, const T* __restrict__ rho,
                                                         const T* __restrict__ s, const T* __restrict__ u,
                                                         const T* __restrict__ z, T* __restrict__ out) {
+  OT_GRID_DEP_WAIT();
   const int n = d.n, nn = n * n, m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
   ROWS_SQUARE(n, i, j)
   for (int k0 = blockIdx.z; k0 < d.K; k0 += gridDim.z) {
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(256) k_kkt_phi_sliced_rows(Dims d, const doubl
                                                              const double* __restrict__ xp,
                                                              const double* __restrict__ yb, bool with_a,
                                                              double* __restrict__ y, double* __restrict__ e) {
+  OT_GRID_DEP_WAIT();
   const int m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
   ROWS_SQUARE(m, I, J)
   for (int jj = blockIdx.z; jj < d.K + 1; jj += gridDim.z) {
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(256) k_kkt_rho_rows(Dims d, const double* __re
                                                       const double* __restrict__ xp, const double* __restrict__ e,
                                                       const double* __restrict__ xr,
                                                       const double* __restrict__ xmean, double* __restrict__ w) {
+  OT_GRID_DEP_WAIT();
   const int n = d.n, nn = n * n, m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
   const double* sr = kc + (i64)(d.K + 1) * 6 * d.N;
   ROWS_SQUARE(n, i, j)
@@ -198,6 +202,7 @@ __global__ void __launch_bounds__(256) k_kkt_phi_rows(Dims d, const T* __restric
                                                       const T* __restrict__ r0, const T* __restrict__ r1,
                                                       const T* __restrict__ xp, const T* __restrict__ xr,
                                                       const T* __restrict__ xmean, bool with_a, T* __restrict__ y) {
+  OT_GRID_DEP_WAIT();
   const int m = d.m, mm = m * m, N = (int)d.N, Nc = (int)d.Nc;
   ROWS_SQUARE(m, I, J)
   for (int jj = blockIdx.z; jj < d.K + 1; jj += gridDim.z) {
@@ -233,11 +238,13 @@ __global__ void __launch_bounds__(256) k_kkt_phi_rows(Dims d, const T* __restric
 // ------------------------------------------------------------------ residual
 __global__ void k_residual_phi_kernel(Dims d, const double* phi, const double* rho, const double* r0,
                                       const double* r1, double* F) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(jj, d.K + 1, c, d.N) F[(i64)jj * d.N + c] = residual_phi(d, phi, rho, r0, r1, jj, c);
 }
 
 __global__ void k_residual_rho_kernel(Dims d, double mu, const double* phi, const double* rho, const double* s,
                                       double* Frho, double* Fs) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k0, d.K, C, d.Nc) {
     i64 i = (i64)k0 * d.Nc + C;
     Frho[i] = residual_rho(d, phi, s, k0, C);
@@ -256,6 +263,7 @@ void k_residual(const Dims& d, double mu, const double* phi, const double* rho, 
 // ------------------------------------------------------------------ KKT operator
 template <typename T>
 __global__ void k_slice_mean_kernel(const T* x, i64 n, T* mean) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   const T* xs = x + (i64)blockIdx.x * n;
   double a = strided_sum(xs, n);
@@ -273,16 +281,19 @@ __global__ void k_slice_mean_kernel(const T* x, i64 n, T* mean) {
 template <typename T>
 __global__ void k_kkt_phi_kernel(Dims d, const T* phi, const T* rho, const T* r0, const T* r1, const T* xp,
                                  const T* xr, const T* xmean, bool with_a, T* y) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(jj, d.K + 1, c, d.N) y[(i64)jj * d.N + c] = kkt_phi(d, phi, rho, r0, r1, xp, xr, xmean, with_a, jj, c);
 }
 
 __global__ void k_kkt_rho_kernel(Dims d, const double* phi, const double* rho, const double* s, const double* xp,
                                  const double* xr, const double* xmean, double* w) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k0, d.K, C, d.Nc) w[(i64)k0 * d.Nc + C] = kkt_rho(d, phi, rho, s, xp, xr, xmean, k0, C);
 }
 
 // y_rho = w - slice mean(w) (P with equal coarse areas); wsum = slice sums of w.
 __global__ void k_project_kernel(double* w, i64 n, double* wsum) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   __shared__ double mean;
   double* ws = w + (i64)blockIdx.x * n;
@@ -303,6 +314,7 @@ __global__ void k_project_kernel(double* w, i64 n, double* wsum) {
 
 __global__ void k_kkt_coef_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
                                   double* kc) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(jj, d.K + 1, c, d.N) {
     double w[3], g[3];
     kkt_edge_coef(d, phi, rho, r0, r1, jj, c, w, g);
@@ -316,6 +328,7 @@ __global__ void k_kkt_coef_kernel(Dims d, const double* phi, const double* rho, 
 }
 
 __global__ void k_kkt_sr_kernel(Dims d, const double* rho, const double* s, double* sr) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, (i64)d.K * d.Nc) sr[i] = d.area_c * s[i] / rho[i];
 }
 
@@ -327,6 +340,7 @@ void k_kkt_coef(const Dims& d, const double* phi, const double* rho, const doubl
 
 // Slice values of the B^T part (kkt_slice_values) into the scratch of kc.
 __global__ void k_kkt_slice_values_kernel(Dims d, const double* xr, const double* xmean, double* yb) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(jj, d.K + 1, C, d.Nc) kkt_slice_values(d, xr, xmean, jj, C, yb);
 }
 
@@ -412,6 +426,7 @@ void k_schur_apply(const Dims& d, const double* phi, const double* rho, const do
 
 template <typename T>
 __global__ void k_atilde_kernel(Dims d, const T* rho, const T* z, T* y) {
+  OT_GRID_DEP_WAIT();
   SLICE_LOOP(k0, d.K, C, d.Nc) y[(i64)k0 * d.Nc + C] = apply_atilde(d, rho, z, k0, C) / (T)d.area_c;
 }
 
@@ -422,6 +437,7 @@ void k_atilde_minv(const Dims& d, const double* rho, const double* z, double* y,
 // ------------------------------------------------------------------ cost and dual value
 __global__ void k_cost_dual_kernel(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
                                    double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sa[32], sb[32];
   i64 tot = (i64)(d.K + 1) * d.N;
   double a = 0.0, b = 0.0;
@@ -445,6 +461,7 @@ __global__ void k_cost_dual_kernel(Dims d, const double* phi, const double* rho,
 }
 
 __global__ void k_cost_dual_finish(const double* partial, int nb, double dt, double* out) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0) return;
   double a = 0.0, b = 0.0;
   for (int q = 0; q < nb; ++q) { a += partial[2 * q]; b += partial[2 * q + 1]; }
@@ -460,12 +477,14 @@ void k_cost_dual(const Dims& d, const double* phi, const double* rho, const doub
 
 // ------------------------------------------------------------------ Newton pieces
 __global__ void k_newton_rhs_phi(const double* Fphi, double* f, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) f[i] = -Fphi[i];
 }
 
 // g~ = -F_rho - |c'| h / rho with h = -(F_s - mu); projected per slice, slice sums kept.
 __global__ void k_newton_rhs_rho(Dims d, const double* Frho, const double* Fs, const double* rho, double* gt,
                                  double* hvec, double* gsum) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   __shared__ double mean;
   i64 base = (i64)blockIdx.x * d.Nc;
@@ -501,6 +520,7 @@ void k_newton_rhs(const Dims& d, const double* Fphi, const double* Frho, const d
 // ds = (h - s drho)/rho; candidate step min over negative directions of -x/dx, times tau.
 __global__ void k_step_kernel(i64 n, const double* rho, const double* s, const double* drho, const double* h,
                               double* ds, double* partial) {
+  OT_GRID_DEP_WAIT();
   __shared__ double sm[32];
   double a = INFINITY;
   GRID_LOOP(i, n) {
@@ -520,6 +540,7 @@ __global__ void k_step_kernel(i64 n, const double* rho, const double* s, const d
 }
 
 __global__ void k_step_finish(const double* partial, int nb, double tau, double* out) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0) return;
   double a = INFINITY;
   for (int q = 0; q < nb; ++q) a = fmin(a, partial[q]);
@@ -535,6 +556,7 @@ void k_step_length(const Dims& d, const double* rho, const double* s, const doub
 
 __global__ void k_update_kernel(i64 Np, i64 Nr, const double* alpha_dev, double a_host, const double* dphi,
                                 const double* drho, const double* ds, double* phi, double* rho, double* s) {
+  OT_GRID_DEP_WAIT();
   double a = alpha_dev ? alpha_dev[0] : a_host;
   GRID_LOOP(i, Np) phi[i] += a * dphi[i];
   GRID_LOOP(i, Nr) {
@@ -551,6 +573,7 @@ void k_update(const Dims& d, const double* alpha_dev, double a_host, const doubl
 
 __global__ void k_shift_const_kernel(int K, double dt, double area_total, const double* gsum, const double* wsum,
                                      double* cshift) {
+  OT_GRID_DEP_WAIT();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double c = 0.0;
   cshift[0] = 0.0;
@@ -566,6 +589,7 @@ void k_shift_constants(const Dims& d, const double* gsum, const double* wsum, do
 }
 
 __global__ void k_rescale_kernel(Dims d, double* rho, const double* mass, double target) {
+  OT_GRID_DEP_WAIT();
   i64 tot = (i64)d.K * d.Nc;
   GRID_LOOP(i, tot) rho[i] *= target / mass[i / d.Nc];
 }
@@ -580,6 +604,7 @@ namespace ot {
 // Initial point (reading R8): rho^k = (1 - k dt) rho_in + k dt rho_f, phi = 0, s = mu0 / rho.
 __global__ void k_init_point_kernel(Dims d, double mu0, const double* r0, const double* r1, double* phi,
                                     double* rho, double* s) {
+  OT_GRID_DEP_WAIT();
   i64 Np = (i64)(d.K + 1) * d.N, Nr = (i64)d.K * d.Nc;
   GRID_LOOP(i, Np) phi[i] = 0.0;
   GRID_LOOP(i, Nr) {
@@ -599,6 +624,7 @@ void k_init_point(const Dims& d, double mu0, const double* r0, const double* r1,
 
 // out = a .* b * scale
 __global__ void k_mul_kernel(const double* a, const double* b, double scale, double* out, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) out[i] = scale * a[i] * b[i];
 }
 void k_mul(const double* a, const double* b, double scale, double* out, i64 n, Stream st) {
@@ -609,6 +635,7 @@ void k_mul(const double* a, const double* b, double scale, double* out, i64 n, S
 // the rho rows projected (slice means removed, slice sums to gsum).
 __global__ void k_adj_rhs_phi(Dims d, const double* phi, const double* rho, const double* r0, const double* r1,
                               double* out) {
+  OT_GRID_DEP_WAIT();
   i64 tot = (i64)(d.K + 1) * d.N;
   GRID_LOOP(i, tot) {
     int jj = (int)(i / d.N);
@@ -617,6 +644,7 @@ __global__ void k_adj_rhs_phi(Dims d, const double* phi, const double* rho, cons
 }
 
 __global__ void k_adj_rhs_rho(Dims d, const double* phi, double* out) {
+  OT_GRID_DEP_WAIT();
   i64 tot = (i64)d.K * d.Nc;
   GRID_LOOP(i, tot) {
     int k0 = (int)(i / d.Nc);
@@ -635,6 +663,7 @@ void k_adjoint_rhs(const Dims& d, const double* phi, const double* rho, const do
 
 // grad_in = dt/4 R_T (grad phi^1)^2 - lambda^T dF/drho_in, grad_f likewise with phi^{K+1}.
 __global__ void k_adj_grad_kernel(Dims d, const double* phi, const double* lam, double* gin, double* gf) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(C, d.Nc) {
     gin[C] = d.dt * kinetic_rho(d, phi, 0, C) - adjoint_boundary(d, phi, lam, 0, 1.0, C);
     gf[C] = d.dt * kinetic_rho(d, phi, d.K, C) - adjoint_boundary(d, phi, lam, d.K, -1.0, C);
@@ -671,6 +700,7 @@ void k_atilde_minv(const Dims& d, const float* rho, const float* z, float* y, St
 
 template <typename A, typename B>
 __global__ void k_convert_kernel(const A* x, B* y, i64 n, double scale) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) y[i] = (B)(scale * (double)x[i]);
 }
 void k_convert(const double* x, float* y, i64 n, double scale, Stream st) {
@@ -682,6 +712,7 @@ void k_convert(const float* x, double* y, i64 n, double scale, Stream st) {
 
 // out (float) = scale * a (float) .* b (double)
 __global__ void k_mul_mixed_kernel(const float* a, const double* b, double scale, float* out, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) out[i] = (float)(scale * (double)a[i] * b[i]);
 }
 void k_mul(const float* a, const double* b, double scale, float* out, i64 n, Stream st) {
@@ -690,6 +721,7 @@ void k_mul(const float* a, const double* b, double scale, float* out, i64 n, Str
 
 // y (float) = (float) c - y (the B^T P^T term), per element
 __global__ void k_rsub_mixed_kernel(const double* c, float* y, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) y[i] = (float)c[i] - y[i];
 }
 void k_rsub(const double* c, float* y, i64 n, Stream st) { launch(k_rsub_mixed_kernel, nblk(n), kT, 0, cs(st), c, y, n); }

@@ -40,6 +40,7 @@ static inline int nblk(i64 n) {
 // Ad[jj N + c] = sum of the three edge weights of fine cell c in slice jj: the
 // diagonal of A^{jj+1} = -div(rho~ grad) (boundary slots carry weight 0).
 __global__ void k_simple_diag_kernel(Dims d, const double* __restrict__ kc, double* __restrict__ Ad) {
+  OT_GRID_DEP_WAIT();
   const i64 n = (i64)(d.K + 1) * d.N;
   GRID_LOOP(i, n) {
     const i64 jj = i / d.N, c = i - jj * d.N;
@@ -53,6 +54,7 @@ __global__ void k_simple_diag_kernel(Dims d, const double* __restrict__ kc, doub
 // of the tridiagonal system described above.
 __global__ void k_simple_line_factor_kernel(Dims d, const double* __restrict__ kc, const double* __restrict__ Ad,
                                             double* __restrict__ inv, double* __restrict__ e) {
+  OT_GRID_DEP_WAIT();
   const i64 C = blockIdx.x * (i64)blockDim.x + threadIdx.x;
   if (C >= d.Nc) return;
   i64 ch[4];
@@ -89,6 +91,7 @@ __global__ void k_simple_line_factor_kernel(Dims d, const double* __restrict__ k
 __global__ void k_simple_line_solve_kernel(Dims d, const double* __restrict__ inv, const double* __restrict__ e,
                                            const double* __restrict__ r, const double* __restrict__ shift, int unit,
                                            double* __restrict__ z) {
+  OT_GRID_DEP_WAIT();
   const i64 C = blockIdx.x * (i64)blockDim.x + threadIdx.x;
   if (C >= d.Nc) return;
   double prev = 0.0, e_prev = 0.0;
@@ -112,6 +115,7 @@ __global__ void k_simple_line_solve_kernel(Dims d, const double* __restrict__ in
 // In-place Cholesky factor (lower, column-major, leading dimension K) of the
 // K x K symmetric positive definite G by one CTA, left-looking by columns.
 __global__ void k_simple_gram_factor_kernel(int K, double* G, int* status) {
+  OT_GRID_DEP_WAIT();
   __shared__ double red[32];
   __shared__ double piv;
   for (int j = 0; j < K; ++j) {
@@ -145,6 +149,7 @@ __global__ void k_simple_gram_factor_kernel(int K, double* G, int* status) {
 // substitution, a column of updates per step).
 __global__ void k_simple_gram_solve_kernel(int K, const double* __restrict__ L, const double* __restrict__ t,
                                            double* __restrict__ lam) {
+  OT_GRID_DEP_WAIT();
   extern __shared__ double x[];
   for (int i = threadIdx.x; i < K; i += blockDim.x) x[i] = t[i];
   __syncthreads();
@@ -168,6 +173,7 @@ __global__ void k_simple_gram_solve_kernel(int K, const double* __restrict__ L, 
 // out = beta * out + alpha * num / den, element-wise.
 __global__ void k_quot_kernel(const double* __restrict__ num, const double* __restrict__ den, double alpha,
                               double* __restrict__ out, double beta, i64 n) {
+  OT_GRID_DEP_WAIT();
   GRID_LOOP(i, n) {
     const double q = alpha * num[i] / den[i];
     out[i] = (beta == 0.0) ? q : beta * out[i] + q;

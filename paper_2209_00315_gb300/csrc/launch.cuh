@@ -1,6 +1,6 @@
 // launch.cuh -- every kernel launch of the library goes through launch(), which
-// counts it (prof::n_launch; into a graph: prof::t_captured) before the <<<>>>
-// launch on the given stream.
+// counts it (prof::n_launch; into a graph: prof::t_captured) and launches it on
+// the given stream (with programmatic dependent launch when dev::pdl is set).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,12 +44,33 @@ __device__ __forceinline__ double strided_sum(const T* xs, long long n) {
   return (double)((a0 + a1) + (a2 + a3));
 }
 
+// First statement of every kernel: wait until the grid this launch depends on
+// has completed and its writes are visible (a no-op for a launch without the
+// programmatic-serialisation attribute).
+#define OT_GRID_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
 template <typename... KArgs, typename... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
   if (prof::capturing)
     ++prof::t_captured;  // counted when the graph runs
   else
     ++prof::n_launch;
+  if (dev::pdl) {
+    // programmatic dependent launch: the grid may be scheduled while its predecessor's last
+    // blocks run; the kernel's OT_GRID_DEP_WAIT keeps the data dependency
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    return;
+  }
   kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
 }
 

@@ -27,6 +27,16 @@ struct Error : std::runtime_error {
 };
 
 namespace dev {
+// Programmatic dependent launch for this thread's launches (set per solve from
+// ot_options.pdl): each kernel may be scheduled while its predecessor's last
+// blocks finish; every kernel begins by waiting for its predecessor's results
+// (griddepcontrol.wait), so the order of work and its results are unchanged.
+extern thread_local bool pdl;
+struct PdlScope {
+  bool saved;
+  explicit PdlScope(bool on) : saved(pdl) { pdl = on; }
+  ~PdlScope() { pdl = saved; }
+};
 void* alloc(size_t bytes);                       // throws Error(OT_ERR_OOM)
 // This thread's later alloc/release become stream-ordered on s (null: plain).
 void set_alloc_stream(Stream s);

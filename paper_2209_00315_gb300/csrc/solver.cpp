@@ -599,6 +599,7 @@ static long long inner_total(Workspace& W, Stream st) {
 
 double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, double tol_rel,
               const double* tol_ref, int nref, Stream st) {
+  dev::PdlScope pdl_scope(opt.pdl != 0);
   Krylov& K = W.outer;
   const i64 n = W.ntot;
   const bool shadow = opt.gs_shadow && K.V32 != nullptr;
@@ -634,7 +635,7 @@ double fgmres(Workspace& W, const ot_options& opt, const double* b, double* x, d
       char key[160];
       snprintf(key, sizeof(key), "fgmres:%d:%d:%d:%d:%d:%d:%d:%.17g:%p:%p:%p:%d:%d", (int)first, m, (int)shadow,
                (int)fp32_reorth, opt.smooth_sweeps, opt.coarse_sweeps, opt.lap_cycles, opt.eps_schur, (const void*)b,
-               (const void*)x, (const void*)tol_ref, opt.schur_max_iter, (int)simple);
+               (const void*)x, (const void*)tol_ref, opt.schur_max_iter, (int)simple + 2 * (opt.pdl != 0));
       std::unique_ptr<dev::Graph>& gp = W.graphs[key];
       if (!gp) {
         gp.reset(new dev::Graph());
@@ -709,6 +710,7 @@ double newton_direction(Workspace& W, const ot_options& opt, double normF, doubl
 
 // ------------------------------------------------------------------ interior point
 int ipm_run(Workspace& W, const ot_options& opt, double mu0, double tol, ot_stats* stats, Stream st) {
+  dev::PdlScope pdl_scope(opt.pdl != 0);
   const Dims& d = W.d;
   const int K = d.K;
   const double area_total = 1.0;

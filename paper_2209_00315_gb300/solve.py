@@ -42,6 +42,8 @@ def main(argv=None):
     p.add_argument("--smooth-sweeps", type=int, default=None, help="multigrid pre/post sweeps per level")
     p.add_argument("--coarse-sweeps", type=int, default=None, help="multigrid sweeps on the coarsest level")
     p.add_argument("--lap-cycles", type=int, default=None, help="V-cycles per slice-Laplacian solve")
+    p.add_argument("--pdl", type=int, choices=[0, 1], default=None,
+                   help="1: programmatic dependent launch (default); 0: plain stream order")
     a = p.parse_args(argv)
 
     from ot_inputs import config_densities
@@ -69,7 +71,7 @@ def main(argv=None):
         extra["precond"] = a.precond
     if a.simple_mu is not None:
         extra["simple_mu"] = a.simple_mu
-    for f in ("smooth_sweeps", "coarse_sweeps", "lap_cycles"):
+    for f in ("smooth_sweeps", "coarse_sweeps", "lap_cycles", "pdl"):
         if getattr(a, f) is not None:
             extra[f] = getattr(a, f)
     opt = capi.default_options(precision=a.precision, verbose=int(a.verbose), **extra)
@@ -96,6 +98,7 @@ def main(argv=None):
         "mu_factor": opt.mu_factor, "mu_final": st["mu"], "graphs": opt.graphs, "gs_shadow": opt.gs_shadow,
         "precond": ["bb", "simple", "hybrid"][opt.precond], "simple_mu": opt.simple_mu,
         "smooth_sweeps": opt.smooth_sweeps, "coarse_sweeps": opt.coarse_sweeps, "lap_cycles": opt.lap_cycles,
+        "pdl": opt.pdl,
         "stage_newton": st["stage_newton"], "stage_outer": st["stage_outer"], "stage_inner": st["stage_inner"],
         "stage_seconds": st["stage_seconds"],
     }))

@@ -68,3 +68,26 @@ def test_captured_newton_direction_equals_uncaptured(gpu_lib):
     for i in range(3):
         assert rel(dirs[1][i], dirs[0][i]) < 1e-12, i
     assert dirs[0][3]["fgmres_iters"] == dirs[1][3]["fgmres_iters"]
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_programmatic_dependent_launch_changes_nothing(gpu_lib, graphs):
+    """ot_options.pdl lets each kernel be scheduled while its predecessor's last
+    blocks finish; every kernel first waits for its predecessor's results, so
+    the iterates are bitwise those of plain stream order, captured or not."""
+    from paper_2209_00315_gb300 import capi
+
+    n = 16
+    _, K, r0, r1 = config_densities("mixN", n)
+    mesh = capi.Mesh(n)
+    r0d, r1d = torch.from_numpy(r0).to(DEV), torch.from_numpy(r1).to(DEV)
+    out = {}
+    for pdl in (0, 1):
+        opt = capi.default_options(precision="mixed", graphs=graphs, pdl=pdl)
+        out[pdl] = capi.ot_ipm_solve(mesh, r0d, r1d, K, options=opt)
+    a, b = out[0], out[1]
+    assert a["stats"]["fgmres_iters"] == b["stats"]["fgmres_iters"]
+    assert a["stats"]["inner_iters"] == b["stats"]["inner_iters"]
+    assert a["cost"] == b["cost"]
+    for key in ("rho", "phi", "s"):
+        assert torch.equal(a[key], b[key]), key
