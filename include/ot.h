@@ -106,7 +106,8 @@ typedef struct {
   int32_t precond;          /* ot_precond: OT_PRECOND_BB (default), OT_PRECOND_SIMPLE or OT_PRECOND_HYBRID.
                                SIMPLE runs in FP64 in both precisions: A^ = Diag(A), its Schur complement
                                solved by GMRES to eps_schur (at most schur_max_iter iterations),
-                               preconditioned by exact solves of its time-line (tridiagonal) part */
+                               preconditioned by exact solves of its time-line (tridiagonal) part;
+                               it needs K <= 1024 (OT_ERR_INVALID_ARG otherwise) */
   double simple_mu;         /* HYBRID: SIMPLE for the stages with mu < simple_mu (1e-5) */
   int32_t pdl;              /* 1 (default): the solver's kernels use programmatic dependent launch (each
                                may be scheduled while its predecessor's last blocks finish, then waits
