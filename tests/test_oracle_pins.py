@@ -408,6 +408,49 @@ def test_simple_application_inverts_its_block_approximation(n, K):
     assert np.abs(P.T @ y - y).max() < 1e-12 * np.abs(y).max()
 
 
+@pytest.mark.parametrize("n,K", [(2, 3), (4, 5)])
+def test_simple_schur_complement_is_its_time_lines_without_potential_gradient(n, K):
+    """SIMPLE's Schur complement -S^ = P C P^T + P B A^-1 B^T P^T (Sec. 4.2, A^ =
+    Diag(A)) couples only the slices of one coarse cell when the potential has no
+    spatial gradient: it is then P L P^T with L block tridiagonal in time per
+    coarse cell C, diagonal |C| s^k/rho^k + w^k_C + w^{k+1}_C and couplings
+    -w^{k+1}_C, w^j_C = sum over the fine cells f of C of |f|^2 / (A^_{j,f} dt^2).
+    This is the operator whose exact inverse on the zero-slice-sum subspace
+    preconditions the GPU's inner SIMPLE solve.  A potential varying in space
+    adds couplings between cells, so the two then differ."""
+    d = ipm.discretise(n, K)
+    rng = np.random.default_rng(40 + n + K)
+    r0 = rng.uniform(0.5, 2, d.Nc)
+    r1 = rng.uniform(0.5, 2, d.Nc)
+    r1 *= (d.t.coarse.area @ r0) / (d.t.coarse.area @ r1)
+    rho = ipm.renormalise(d, rng.uniform(0.5, 2, K * d.Nc), r0)
+    s = rng.uniform(0.5, 2, K * d.Nc)
+    P = d.P_block()
+
+    def neg_schur(phi):
+        Ad = d.A_block(rho, r0, r1).diagonal()
+        Bp = (P @ d.B_block(phi)).tocsr()
+        return (P @ d.C_block(rho, s) @ P.T + Bp @ sp.diags(1.0 / Ad) @ Bp.T).toarray(), Ad
+
+    def time_lines(Ad):
+        f2 = d.t.fine.area ** 2 / d.dt ** 2
+        w = np.array([d.J.T @ (f2 / Ad[j * d.N:(j + 1) * d.N]) for j in range(K + 1)])   # (K+1) x N'
+        cdiag = (np.tile(d.t.coarse.area, K) * s / rho).reshape(K, d.Nc)
+        L = sp.diags((cdiag + w[:-1] + w[1:]).ravel())
+        if K > 1:
+            off = -w[1:-1].ravel()
+            L = L + sp.diags(off, d.Nc) + sp.diags(off, -d.Nc)
+        return (P @ L @ P.T).toarray()
+
+    flat = np.repeat(rng.standard_normal(K + 1), d.N)          # constant in space on every slice
+    S, Ad = neg_schur(flat)
+    T = time_lines(Ad)
+    assert np.abs(S - T).max() < 1e-12 * np.abs(S).max()
+    wavy = 0.3 * rng.standard_normal((K + 1) * d.N)
+    S, Ad = neg_schur(wavy)
+    assert np.abs(S - time_lines(Ad)).max() > 1e-3 * np.abs(S).max()
+
+
 def _gmres_right(apply_op, b, apply_prec, tol=1e-5, maxit=300):
     """Iterations of right-preconditioned GMRES (dense, two Gram-Schmidt passes) to ||r|| <= tol ||b||."""
     beta = np.linalg.norm(b)
