@@ -435,90 +435,12 @@ static inline int pcr_kpl(int S) { return S <= 32 ? 1 : (S <= 64 ? 2 : (S <= 128
 // Tiled line smoother: a CTA of TC warps owns TC consecutive cells of one
 // colour.  Their K-slice systems are gathered with row loads of TC cells into
 // a padded [K][TC+1] shared tile (each thread loads its KPL rows before using
-// any), warp w solves column w by PCR, and the solutions leave through the
-// same tile.  TC = 8 keeps many CTAs on small levels; TC = 16 gives 64-byte
-// row segments (FP32) on large ones.
-// The three stages of one tile, run by the 32 TC threads (tid) of a CTA on
-// their own shared tile (3 S (TC+1) values), with a barrier of those threads
-// between stages.  tile: index of the first cell / TC.
-template <typename T, int TC, int KPL, int MODE>
-__device__ __forceinline__ void tile_gather(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color,
-                                            int tile, int tid, T* tsm) {
-  constexpr int P = TC + 1;
-  T* sd = tsm;           // [S][P] diagonal
-  T* sr = sd + S * P;    // [S][P] right-hand side, then solution
-  T* st = sr + S * P;    // [S][P] tau
-  const int sq = L.m * L.m, ld = (int)L.ld;
-  const int j = tid % TC, row0 = tid / TC;  // rows row0, row0 + 32, ...
-  const int cell = tile * TC + j;
-  const bool live = cell < sq;
-  i64 nb[3] = {-1, -1, -1};
-  const int c = color * sq + cell;
-  if (live) neighbours(L.m, decode(L.m, c), nb);
-  T tau[KPL], bb[KPL], al[KPL][3], xn[KPL][3];
-#pragma unroll
-  for (int q = 0; q < KPL; ++q) {
-    const int k = row0 + 32 * q;
-    tau[q] = 0;
-    bb[q] = 0;
-#pragma unroll
-    for (int sl = 0; sl < 3; ++sl) al[q][sl] = 0, xn[q][sl] = 0;
-    if (live && k < S) {
-      const int o = k * ld;
-      tau[q] = L.tau[o + c];
-      bb[q] = L.b[o + c];
-#pragma unroll
-      for (int sl = 0; sl < 3; ++sl) {
-        al[q][sl] = L.alpha[(sl * S + k) * ld + c];
-        if (MODE != kSweepFromZero && nb[sl] >= 0) xn[q][sl] = sweep_neighbour<T, MODE>(L, Lc, k, (int)nb[sl]);
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < KPL; ++q) {
-    const int k = row0 + 32 * q;
-    if (k >= S) continue;
-    T dg = live ? 2 * tau[q] : (T)1, rhs = bb[q];
-#pragma unroll
-    for (int sl = 0; sl < 3; ++sl) {
-      dg += al[q][sl];
-      if (MODE != kSweepFromZero) rhs += al[q][sl] * xn[q][sl];
-    }
-    sd[k * P + j] = dg;
-    sr[k * P + j] = rhs;
-    st[k * P + j] = tau[q];
-  }
-}
-
-template <typename T, int TC, int KPL>
-__device__ __forceinline__ void tile_solve(int S, int tid, T* tsm) {
-  constexpr int P = TC + 1;
-  T* sd = tsm;
-  T* sr = sd + S * P;
-  T* st = sr + S * P;
-  const int lane = tid & 31, col = tid >> 5;
-  T a[KPL], d[KPL], cc[KPL], r[KPL];
-#pragma unroll
-  for (int q = 0; q < KPL; ++q) {
-    int k = lane + 32 * q;
-    if (k < S) {
-      T tau = st[k * P + col];
-      d[q] = sd[k * P + col];
-      r[q] = sr[k * P + col];
-      a[q] = (k > 0) ? -tau : (T)0;
-      cc[q] = (k < S - 1) ? -tau : (T)0;
-    } else {
-      d[q] = 1; r[q] = 0; a[q] = 0; cc[q] = 0;
-    }
-  }
-  pcr_solve<T, KPL>(a, d, cc, r, lane);
-#pragma unroll
-  for (int q = 0; q < KPL; ++q) {
-    int k = lane + 32 * q;
-    if (k < S) sr[k * P + col] = mg_div(r[q], d[q]);
-  }
-}
-
+// any), warp w solves column w through the line's stored Thomas factors, and
+// the solutions leave through the same tile.  TC = 8 keeps many CTAs on small
+// levels; TC = 16 gives 64-byte row segments (FP32) on large ones.  The stages
+// of one tile are run by the 32 TC threads (tid) of a CTA on their own shared
+// tile (3 S (TC+1) values), with a barrier between stages.  tile: index of the
+// first cell / TC.
 template <typename T, int TC, int KPL>
 __device__ __forceinline__ void tile_store(int S, const LevelView<T>& L, int color, int tile, int tid, const T* tsm) {
   constexpr int P = TC + 1;
@@ -535,18 +457,6 @@ __device__ __forceinline__ void tile_store(int S, const LevelView<T>& L, int col
   }
 }
 
-template <typename T, int TC, int KPL, int MODE>
-__global__ void __launch_bounds__(32 * TC) k_line_pcr_tile_kernel(int S, LevelView<T> L, LevelView<T> Lc, int color) {
-  OT_GRID_DEP_WAIT();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tsm = reinterpret_cast<T*>(smem_raw);
-  tile_gather<T, TC, KPL, MODE>(S, L, Lc, color, blockIdx.x, threadIdx.x, tsm);
-  __syncthreads();
-  tile_solve<T, TC, KPL>(S, threadIdx.x, tsm);
-  __syncthreads();
-  tile_store<T, TC, KPL>(S, L, color, blockIdx.x, threadIdx.x, tsm);
-}
-
 // Thomas factors of every line of a level in device memory (once per Newton step).
 template <typename T>
 __global__ void k_line_factor_kernel(int S, LevelView<T> L) {
@@ -561,8 +471,9 @@ void k_mg_line_factor(int S, const LevelView<T>& L, Stream st) {
 }
 
 // The tile stages with stored factors: the gather writes the substitution
-// coefficients A = tau/den, B = r/den, C = -cp (tile_gather's right-hand side
-// r), the solve runs scan_tridiag on contiguous rows per lane.
+// coefficients A = tau/den, B = r/den, C = -cp (r: the line's right-hand side
+// with the neighbour values of the sweep mode), the solve runs scan_tridiag on
+// contiguous rows per lane.
 template <typename T, int TC, int KPL, int MODE>
 __device__ __forceinline__ void tile_gather_fac(int S, const LevelView<T>& L, const LevelView<T>& Lc, int color,
                                                 int tile, int tid, T* tsm) {
@@ -661,31 +572,20 @@ static void launch_tile_tc(int S, const LevelView<T>& L, const LevelView<T>& Lc,
   const i64 sq = (i64)L.m * L.m;
   const int blocks = (int)((sq + TC - 1) / TC);
   const size_t tile = 3 * (size_t)S * (TC + 1) * sizeof(T);
-  if (L.fac) {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-    if (kpl == 1)
-      launch(k_line_scan_tile_kernel<T, TC, 1, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
-    else if (kpl == 2)
-      launch(k_line_scan_tile_kernel<T, TC, 2, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
-    else
-      launch(k_line_scan_tile_kernel<T, TC, 4, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
-    return;
-  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   if (kpl == 1)
-    launch(k_line_pcr_tile_kernel<T, TC, 1, MODE>, blocks, 32 * TC, tile, reinterpret_cast<cudaStream_t>(st), S, L, Lc,
-           color);
+    launch(k_line_scan_tile_kernel<T, TC, 1, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
   else if (kpl == 2)
-    launch(k_line_pcr_tile_kernel<T, TC, 2, MODE>, blocks, 32 * TC, tile, reinterpret_cast<cudaStream_t>(st), S, L, Lc,
-           color);
+    launch(k_line_scan_tile_kernel<T, TC, 2, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
   else
-    launch(k_line_pcr_tile_kernel<T, TC, 4, MODE>, blocks, 32 * TC, tile, reinterpret_cast<cudaStream_t>(st), S, L, Lc,
-           color);
+    launch(k_line_scan_tile_kernel<T, TC, 4, MODE>, blocks, 32 * TC, tile, s, S, L, Lc, color);
 }
 
-// The tile width for this shape, or 0 if no tiled sweep applies (K > 128, a tile
-// beyond 48 KB of shared memory, or indices beyond 32 bits).
+// The tile width for this shape, or 0 if no tiled sweep applies (no stored line
+// factors, K > 128, a tile beyond 48 KB of shared memory, or indices beyond 32 bits).
 template <typename T>
 static int tile_width(int S, const LevelView<T>& L) {
+  if (!L.fac) return 0;
   int tc = tile_cells((i64)L.m * L.m);
   if (3 * (size_t)S * (tc + 1) * sizeof(T) > 48 * 1024) tc = 8;
   if (pcr_kpl(S) == 0 || 3 * (size_t)S * (tc + 1) * sizeof(T) > 48 * 1024 || 3 * (i64)S * L.ld >= (1ll << 31)) return 0;
