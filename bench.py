@@ -76,6 +76,19 @@ def group_traffic(workload: str, group: str, algorithmic_per_op: float):
     return None if r is None else r * algorithmic_per_op
 
 
+def cpu_model() -> str:
+    """The host CPU's model name from lscpu (e.g. Neoverse-V2), or '' if unavailable."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for line in out.splitlines():
+        if line.strip().lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    return ""
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -236,7 +249,8 @@ def oracle_baseline(threads: int, newton_steps: int = WORKLOAD_NEWTON_STEPS, sam
     import platform
     return {"value": per_step * newton_steps, "unit": "s", "cores": threads, "kind": "oracle",
             "extrapolated": True, "sample": sample, "per_newton_step_s": per_step, "growth_exponent": p,
-            "sample_points": pts, "cpu": platform.processor() or platform.machine(), "host_cores": os.cpu_count()}
+            "sample_points": pts, "cpu": cpu_model() or platform.processor() or platform.machine(),
+            "host_cores": os.cpu_count()}
 
 
 def run_reference(args, world, rank):
