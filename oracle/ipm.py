@@ -30,12 +30,17 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .mesh import two_level_square
+from .mesh import one_level_cube, two_level_square
 from .operators import Discretisation
 
 
 def discretise(n: int, K: int) -> Discretisation:
     return Discretisation(two_level_square(n), K)
+
+
+def discretise_cube(n: int, K: int) -> Discretisation:
+    """The 3D Cartesian variant (the paper's test 4): n^3 cubes, J = I."""
+    return Discretisation(one_level_cube(n), K)
 
 
 # ------------------------------------------------------------------ residual

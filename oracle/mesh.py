@@ -1,4 +1,4 @@
-"""Generic triangle meshes and TPFA geometry for the oracle (Sec. 2.1 of the paper).
+"""Generic triangle meshes, Cartesian cube grids and TPFA geometry for the oracle (Sec. 2.1 of the paper).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -186,3 +186,66 @@ def two_level_square(n: int) -> TwoLevelMesh:
     perm = canonical_square_order(fxy, ftri, 2 * n)
     fine = build_mesh(fxy, ftri[perm])
     return TwoLevelMesh(coarse, fine, parent[perm], n)
+
+
+# ---------------------------------------------------------------- cube grids (3D)
+@dataclass
+class CubeMesh:
+    """A uniform grid of n^3 cubes of side h = 1/n on [0,1]^3, with the same
+    TPFA fields as TriMesh so that the operators apply unchanged: `area` holds
+    the cell measure h^3, each interior face is an `edge` with measure
+    edge_len = h^2, cell-point distance edge_dist = h and weight 1/2 (the
+    cube centres are the cell points; every face is orthogonal to the segment
+    joining them)."""
+
+    n: int
+    area: np.ndarray        # (nc,) cell volumes
+    centre: np.ndarray      # (nc, 3) cube centres
+    bary: np.ndarray        # (nc, 3) the same points
+    edge_cells: np.ndarray  # (nf, 2) [lower, upper] cell along the face normal
+    edge_len: np.ndarray    # (nf,) face areas
+    edge_dist: np.ndarray   # (nf,) distance between the two centres
+    edge_lambda: np.ndarray  # (nf,) 1/2
+    degenerate: np.ndarray  # (nf,) False
+    edge_axis: np.ndarray   # (nf,) 0, 1, 2: normal direction x, y, z
+
+    @property
+    def ncell(self) -> int:
+        return self.area.shape[0]
+
+    @property
+    def nedge(self) -> int:
+        return self.edge_cells.shape[0]
+
+
+def cube_grid(n: int) -> CubeMesh:
+    """n^3 cubes, cell (i, j, k) at index (k n + j) n + i (x fastest)."""
+    h = 1.0 / n
+    idx = lambda i, j, k: (k * n + j) * n + i  # noqa: E731
+    g = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    centre = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    cells, axes = [], []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                if i + 1 < n:
+                    cells.append((idx(i, j, k), idx(i + 1, j, k)))
+                    axes.append(0)
+                if j + 1 < n:
+                    cells.append((idx(i, j, k), idx(i, j + 1, k)))
+                    axes.append(1)
+                if k + 1 < n:
+                    cells.append((idx(i, j, k), idx(i, j, k + 1)))
+                    axes.append(2)
+    nf = len(cells)
+    edge_cells = np.array(cells, dtype=np.int64).reshape(-1, 2)
+    return CubeMesh(n, np.full(n ** 3, h ** 3), centre, centre.copy(), edge_cells, np.full(nf, h * h),
+                    np.full(nf, h), np.full(nf, 0.5), np.zeros(nf, dtype=bool), np.array(axes, dtype=np.int64))
+
+
+def one_level_cube(n: int) -> TwoLevelMesh:
+    """The Cartesian case of the paper's test 4: density and potential on the same
+    n^3 grid, so the injection J is the identity."""
+    m = cube_grid(n)
+    return TwoLevelMesh(m, m, np.arange(m.ncell, dtype=np.int64), n)

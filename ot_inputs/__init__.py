@@ -18,6 +18,10 @@ below by a floor) and the seeded mixtures used for the larger workloads:
   then scaled so that sum_cells |cell| * value = 1.
 Cell averages use the three-edge-midpoint rule (exact for quadratics) on the
 16 triangles of a twice-repeated midpoint split of each cell.
+
+The 3D Cartesian variant (test 4 of Section 4.1) uses n^3 cubes of side 1/n,
+cube (i, j, k) at index (k n + j) n + i, with cell averages by the tensor
+3-point Gauss-Legendre rule in each direction.
 """
 from __future__ import annotations
 
@@ -31,6 +35,8 @@ __all__ = [
     "config_densities",
     "batched_problem_specs",
     "mass_preserving_directions",
+    "make_cube_density",
+    "cube_config_densities",
 ]
 
 
@@ -146,3 +152,34 @@ def mass_preserving_directions(n: int, count: int, seed: int) -> np.ndarray:
     v -= v.mean(1, keepdims=True)
     v /= np.abs(v).max(1, keepdims=True)
     return v
+
+
+def make_cube_density(n: int, centres, sigmas, weights, floor: float) -> np.ndarray:
+    """Floored, unit-mass cell averages of sum_g w_g N(c_g, sigma_g^2 I) on n^3 cubes."""
+    h = 1.0 / n
+    nodes = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)])
+    wts = np.array([5.0, 8.0, 5.0]) / 18.0          # Gauss-Legendre on [0, 1] after the map below
+    g = np.arange(n) * h
+    pts = (g[:, None] + h * (0.5 + 0.5 * nodes)[None, :]).ravel()   # (3n,) quadrature abscissae
+    w1 = np.tile(wts, n)
+    val = np.zeros((n, n, n))
+    for c, s, w in zip(centres, sigmas, weights):
+        f = [np.exp(-((pts - c[a]) ** 2) / (2.0 * s * s)) * w1 for a in range(3)]
+        fx, fy, fz = (fa.reshape(n, 3).sum(1) for fa in f)   # per-cell 1D averages
+        val += w * np.einsum("k,j,i->kji", fz, fy, fx) / (2.0 * np.pi * s * s) ** 1.5
+    v = np.maximum(val.ravel(), floor)
+    return v / (h ** 3 * v.sum())
+
+
+def cube_config_densities(name: str, n: int | None = None):
+    """(n, K, rho_in, rho_f) for the 3D test: Gaussians sigma = 0.1 at
+    (0.3,0.3,0.3) -> (0.7,0.7,0.7), floor 1e-3 (test 4 of Section 4.1).
+    'gauss_cube8': 8^3 cubes, K + 1 = 8 time intervals; 'gauss_cubeN': n^3 (argument), K + 1 = n."""
+    if name == "gauss_cube8":
+        n = 8
+    elif name != "gauss_cubeN":
+        raise KeyError(name)
+    K = n - 1
+    r0 = make_cube_density(n, [(0.3, 0.3, 0.3)], [0.1], [1.0], 1e-3)
+    r1 = make_cube_density(n, [(0.7, 0.7, 0.7)], [0.1], [1.0], 1e-3)
+    return n, K, r0, r1
