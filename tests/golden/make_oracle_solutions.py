@@ -12,6 +12,7 @@ one constant, Sec. 3.1, fixed here by zero M-weighted space-time mean).
 
   python tests/golden/make_oracle_solutions.py fd32        # 32x32 squares, K=16, seeds 6/7
   python tests/golden/make_oracle_solutions.py mixN:24     # 24x24 squares, K=12, seeds 2/3
+  python tests/golden/make_oracle_solutions.py gauss_cube8 # 3D: 8^3 cubes, K=7 (test 4)
 
 Output: tests/golden/<name>_oracle.npz with rho (K N'), phi ((K+1) N, gauged),
 s (K N'), cost, dual, mu, newton_steps and the per-stage Newton counts.
@@ -29,19 +30,24 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 from oracle import ipm  # noqa: E402
-from ot_inputs import config_densities  # noqa: E402
+from ot_inputs import config_densities, cube_config_densities  # noqa: E402
 
 FINAL_NEWTON_TOL = 1e-11
 
 
 def write(name: str) -> str:
-    """name: a workload of ot_inputs.config_densities, or mixN:<n> (n x n squares, K = n/2)."""
+    """name: a workload of ot_inputs.config_densities, mixN:<n> (n x n squares, K = n/2), or
+    a 3D workload of ot_inputs.cube_config_densities."""
     if name.startswith("mixN:"):
         n, K, r0, r1 = config_densities("mixN", int(name.split(":")[1]))
         name = f"mix{n}"
+        d = ipm.discretise(n, K)
+    elif name.startswith("gauss_cube"):
+        n, K, r0, r1 = cube_config_densities(name)
+        d = ipm.discretise_cube(n, K)
     else:
         n, K, r0, r1 = config_densities(name)
-    d = ipm.discretise(n, K)
+        d = ipm.discretise(n, K)
     t0 = time.perf_counter()
     res = ipm.ipm_solve(d, r0, r1, ipm.IPMOptions(final_newton_tol=FINAL_NEWTON_TOL))
     sec = time.perf_counter() - t0

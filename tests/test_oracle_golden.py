@@ -11,12 +11,21 @@ import numpy as np
 import pytest
 
 from oracle import ipm
-from ot_inputs import config_densities
+from ot_inputs import config_densities, cube_config_densities
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
-# stored file -> the workload it was solved on (ot_inputs.config_densities arguments)
-STORED = {"fd32": ("fd32",), "mix24": ("mixN", 24)}
+# stored file -> the workload it was solved on (ot_inputs.config_densities arguments; the 3D
+# workload of the paper's test 4 through cube_config_densities)
+STORED = {"fd32": ("fd32",), "mix24": ("mixN", 24), "gauss_cube8": ("gauss_cube8",)}
+
+
+def _workload(name):
+    if name.startswith("gauss_cube"):
+        n, K, r0, r1 = cube_config_densities(*STORED[name])
+        return n, K, r0, r1, ipm.discretise_cube(n, K)
+    n, K, r0, r1 = config_densities(*STORED[name])
+    return n, K, r0, r1, ipm.discretise(n, K)
 
 
 @pytest.mark.parametrize("name", sorted(STORED))
@@ -26,9 +35,8 @@ def test_stored_solution_is_a_converged_oracle_point(name):
     recomputes, the duality gap is the barrier's mu |Omega| K/(K+1) (Eq. 3.9 at
     a solution of the barrier problem) and phi carries the zero-mean gauge."""
     g = np.load(os.path.join(GOLDEN, f"{name}_oracle.npz"))
-    n, K, r0, r1 = config_densities(*STORED[name])
+    n, K, r0, r1, d = _workload(name)
     assert (n, K) == (int(g["n"]), int(g["K"]))
-    d = ipm.discretise(n, K)
     phi, rho, s, mu = g["phi"], g["rho"], g["s"], float(g["mu"])
     F = ipm.residual(d, phi, rho, s, r0, r1, mu)
     assert ipm.residual_norm(F) < 1e-10

@@ -229,12 +229,18 @@ def test_kernel_of_jacobian_is_global_constant():
     assert np.abs(Jm @ e).max() < 1e-12
 
 
+def _disc(geom, n, K):
+    """The 2D two-level triangle discretisation or the 3D cube grid of test 4."""
+    return ipm.discretise(n, K) if geom == "tri" else ipm.discretise_cube(n, K)
+
+
 # ------------------------------------------------------- projected system
-@pytest.mark.parametrize("n,K", [(1, 1), (2, 2), (2, 3)])
-def test_projected_system_reproduces_newton_direction(n, K):
+@pytest.mark.parametrize("geom,n,K", [("tri", 1, 1), ("tri", 2, 2), ("tri", 2, 3), ("cube", 2, 2)])
+def test_projected_system_reproduces_newton_direction(geom, n, K):
     """The projected system (Sec. 4.3.1) plus the per-slice constants of the
-    splitting (reading R10) reproduces the exact Newton direction (dense LU)."""
-    d = ipm.discretise(n, K)
+    splitting (reading R10) reproduces the exact Newton direction (dense LU),
+    on triangles and on the cube grid of the 3D variant."""
+    d = _disc(geom, n, K)
     rng = np.random.default_rng(7 + n + K)
     r0 = rng.uniform(0.5, 2, d.Nc)
     r1 = rng.uniform(0.5, 2, d.Nc)
@@ -345,8 +351,8 @@ def test_btilde_is_the_block_transpose_of_B_on_coarse_functions(n, K):
             assert np.abs(diff - want).max() < 1e-13 * scale
 
 
-@pytest.mark.parametrize("n,K", [(2, 2), (3, 3)])
-def test_exact_bb_application_solves_its_triangular_factor(n, K):
+@pytest.mark.parametrize("geom,n,K", [("tri", 2, 2), ("tri", 3, 3), ("cube", 2, 2)])
+def test_exact_bb_application_solves_its_triangular_factor(geom, n, K):
     """With exact inner solves the BB application returns (x, y) with
       * y the solution of the approximated Schur system of Eq. (schur-linear-system),
         P (C - B M^-1 B~ A~^+ M') P^T y = -d for d in the range of P, built here
@@ -354,8 +360,9 @@ def test_exact_bb_application_solves_its_triangular_factor(n, K):
         and y = M'^-1 A~ z that the application uses;
       * y in the range of P^T, as Sec. 4.3.3 requires of the solution;
       * x from the first block row of the projected system, A x = c - B^T P^T y
-        up to per-slice constants (the range of A), with zero slice means."""
-    d = ipm.discretise(n, K)
+        up to per-slice constants (the range of A), with zero slice means.
+    On triangles and on the cube grid of the 3D variant."""
+    d = _disc(geom, n, K)
     rng = np.random.default_rng(40 + n + K)
     r0 = rng.uniform(0.5, 2, d.Nc)
     r1 = rng.uniform(0.5, 2, d.Nc)
@@ -382,13 +389,13 @@ def test_exact_bb_application_solves_its_triangular_factor(n, K):
     assert np.abs(x.reshape(K + 1, d.N).mean(axis=1)).max() < 1e-12 * np.abs(x).max()
 
 
-@pytest.mark.parametrize("n,K", [(2, 2), (3, 3)])
-def test_simple_application_inverts_its_block_approximation(n, K):
+@pytest.mark.parametrize("geom,n,K", [("tri", 2, 2), ("tri", 3, 3), ("cube", 2, 3)])
+def test_simple_application_inverts_its_block_approximation(geom, n, K):
     """The three SIMPLE factors (Sec. 4.2) multiply to the inverse of the projected
     system with A replaced by Diag(A): u = (x, y) solves
     [Diag(A), B^T P^T; P B, -P C P^T] u = (c; d) for d in the range of P,
     checked against that matrix assembled from the projected system's blocks."""
-    d = ipm.discretise(n, K)
+    d = _disc(geom, n, K)
     rng = np.random.default_rng(60 + n + K)
     r0 = rng.uniform(0.5, 2, d.Nc)
     r1 = rng.uniform(0.5, 2, d.Nc)
@@ -408,8 +415,8 @@ def test_simple_application_inverts_its_block_approximation(n, K):
     assert np.abs(P.T @ y - y).max() < 1e-12 * np.abs(y).max()
 
 
-@pytest.mark.parametrize("n,K", [(2, 3), (4, 5)])
-def test_simple_schur_complement_is_its_time_lines_without_potential_gradient(n, K):
+@pytest.mark.parametrize("geom,n,K", [("tri", 2, 3), ("tri", 4, 5), ("cube", 3, 4)])
+def test_simple_schur_complement_is_its_time_lines_without_potential_gradient(geom, n, K):
     """SIMPLE's Schur complement -S^ = P C P^T + P B A^-1 B^T P^T (Sec. 4.2, A^ =
     Diag(A)) couples only the slices of one coarse cell when the potential has no
     spatial gradient: it is then P L P^T with L block tridiagonal in time per
@@ -418,7 +425,7 @@ def test_simple_schur_complement_is_its_time_lines_without_potential_gradient(n,
     This is the operator whose exact inverse on the zero-slice-sum subspace
     preconditions the GPU's inner SIMPLE solve.  A potential varying in space
     adds couplings between cells, so the two then differ."""
-    d = ipm.discretise(n, K)
+    d = _disc(geom, n, K)
     rng = np.random.default_rng(40 + n + K)
     r0 = rng.uniform(0.5, 2, d.Nc)
     r1 = rng.uniform(0.5, 2, d.Nc)
