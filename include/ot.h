@@ -54,10 +54,15 @@ typedef enum {
   OT_ERR_OOM = 8                /* device allocation failed */
 } ot_status;
 
-typedef enum { OT_MESH_STRUCTURED_SQUARE = 0 } ot_mesh_kind;
+typedef enum { OT_MESH_STRUCTURED_SQUARE = 0, OT_MESH_CARTESIAN_CUBE = 1 } ot_mesh_kind;
 
 /* Mesh description.  STRUCTURED_SQUARE: n squares per side; n = 2^a b with
- * b <= 11 (the multigrid hierarchy coarsens while the side is even). */
+ * b <= 11 (the multigrid hierarchy coarsens while the side is even).
+ * CARTESIAN_CUBE: the 3D variant of test 4 (Sec. 4.1): n^3 cubes of side 1/n
+ * on [0,1]^3, 1 <= n <= 1024, density and potential on the same grid (J = I),
+ * cube (i, j, k) at index (k n + j) n + i; it supports the operator-level calls
+ * ot_residual, ot_kkt_apply and ot_cost_dual (every solver entry point returns
+ * OT_ERR_INVALID_ARG for it). */
 typedef struct {
   int32_t kind;
   int32_t n;

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libotgb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CUDA_SOURCES = ["k_la.cu", "k_ops.cu", "k_mg.cu", "k_krylov.cu", "k_simple.cu"]
+CUDA_SOURCES = ["k_la.cu", "k_ops.cu", "k_mg.cu", "k_krylov.cu", "k_simple.cu", "k_cube.cu"]
 HOST_SOURCES = ["solver.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -158,13 +158,19 @@ def _stream(stream) -> int:
     return 0
 
 
-class Mesh:
-    """Owner of an ot_mesh (structured unit-square mesh with n x n squares)."""
+OT_MESH_STRUCTURED_SQUARE, OT_MESH_CARTESIAN_CUBE = 0, 1
 
-    def __init__(self, n: int):
+
+class Mesh:
+    """Owner of an ot_mesh: the structured unit-square mesh with n x n squares
+    (kind "square"), or the 3D grid of n^3 cubes of test 4 (kind "cube", operator-level
+    calls only)."""
+
+    def __init__(self, n: int, kind: str = "square"):
         self._lib = load()
         self._h = _P()
-        desc = ot_mesh_desc(0, int(n))
+        self.kind = kind
+        desc = ot_mesh_desc({"square": OT_MESH_STRUCTURED_SQUARE, "cube": OT_MESH_CARTESIAN_CUBE}[kind], int(n))
         _check(self._lib.ot_mesh_create(C.byref(desc), C.byref(self._h)))
         self.n = int(n)
         nc, nf, ne = C.c_int64(), C.c_int64(), C.c_int64()

@@ -21,8 +21,24 @@ using ot::Workspace;
 namespace dev = ot::dev;
 
 struct ot_mesh {
+  int kind = OT_MESH_STRUCTURED_SQUARE;
   int n = 0;
   std::map<std::pair<int, int>, std::unique_ptr<Workspace>> ws;
+};
+
+// The 3D Cartesian variant runs its operator-level calls on scratch of its own.
+static bool is_cube(const ot_mesh* m) { return m && m->kind == OT_MESH_CARTESIAN_CUBE; }
+struct CubeScratch {
+  double* dev = nullptr;   // max(2 K, 2 N) + 2 doubles
+  double* host = nullptr;  // 2 doubles (pinned)
+  explicit CubeScratch(size_t n) {
+    dev = (double*)dev::alloc(sizeof(double) * n);
+    host = (double*)dev::host_alloc(2 * sizeof(double));
+  }
+  ~CubeScratch() {
+    dev::release(dev);
+    dev::host_release(host);
+  }
 };
 
 static thread_local std::string g_err;
@@ -118,6 +134,7 @@ static ot_options resolve(const ot_options* o) {
 
 static Workspace& workspace(ot_mesh* m, int K, const ot_options& o) {
   require(m != nullptr, "mesh is NULL");
+  require(!is_cube(m), "3D Cartesian meshes support only ot_residual, ot_kkt_apply and ot_cost_dual");
   require(K >= 1 && K <= 4096, "K must be in [1, 4096]");
   auto key = std::make_pair(K, o.precision);
   auto it = m->ws.find(key);
@@ -202,9 +219,13 @@ extern "C" {
 ot_status ot_mesh_create(const ot_mesh_desc* desc, ot_mesh** out) {
   OT_TRY
   require(desc && out, "NULL argument");
-  require(desc->kind == OT_MESH_STRUCTURED_SQUARE, "unsupported mesh kind");
-  require(supported_side(desc->n), "n must be 2^a * b with b <= 11 and n <= 4096");
+  require(desc->kind == OT_MESH_STRUCTURED_SQUARE || desc->kind == OT_MESH_CARTESIAN_CUBE, "unsupported mesh kind");
+  if (desc->kind == OT_MESH_STRUCTURED_SQUARE)
+    require(supported_side(desc->n), "n must be 2^a * b with b <= 11 and n <= 4096");
+  else
+    require(desc->n >= 1 && desc->n <= 1024, "cube grids need 1 <= n <= 1024");
   ot_mesh* m = new ot_mesh();
+  m->kind = desc->kind;
   m->n = desc->n;
   *out = m;
   return OT_OK;
@@ -218,6 +239,14 @@ ot_status ot_mesh_info(const ot_mesh* mesh, int64_t* n_coarse, int64_t* n_fine, 
   OT_TRY
   require(mesh != nullptr, "mesh is NULL");
   i64 n = mesh->n, m = 2 * n;
+  if (is_cube(mesh)) {  // one grid of n^3 cubes, 3 n^2 (n - 1) interior faces
+    if (n_coarse) *n_coarse = n * n * n;
+    if (n_fine) *n_fine = n * n * n;
+    if (n_edges_fine) *n_edges_fine = 3 * n * n * (n - 1);
+    if (coarse_areas)
+      for (i64 i = 0; i < n * n * n; ++i) coarse_areas[i] = 1.0 / (double)(n * n * n);
+    return OT_OK;
+  }
   if (n_coarse) *n_coarse = 2 * n * n;
   if (n_fine) *n_fine = 2 * m * m;
   if (n_edges_fine) *n_edges_fine = 3 * m * m - 2 * m;
@@ -491,6 +520,7 @@ ot_status ot_tune_newton(ot_mesh* mesh, int32_t K, double mu, const double* phi,
 // Any cached workspace of this K serves as scratch for the operator-level calls.
 static Workspace& op_workspace(ot_mesh* mesh, int K) {
   require(mesh != nullptr, "mesh is NULL");
+  require(!is_cube(mesh), "3D Cartesian meshes support only ot_residual, ot_kkt_apply and ot_cost_dual");
   for (auto& kv : mesh->ws)
     if (kv.first.first == K) return *kv.second;
   ot_options o;
@@ -504,6 +534,24 @@ ot_status ot_residual(ot_mesh* mesh, int32_t K, double mu, const double* phi, co
   OT_TRY
   require(mesh && phi && rho && s && rho_in && rho_f && F_phi && F_rho && F_s, "NULL argument");
   Stream st = cuda_stream;
+  if (is_cube(mesh)) {
+    require(K >= 1 && K <= 4096, "K must be in [1, 4096]");
+    const ot::CubeDims d = ot::make_cube_dims(mesh->n, K);
+    ot::k_cube_residual(d, mu, phi, rho, s, rho_in, rho_f, F_phi, F_rho, F_s, st);
+    if (norms) {
+      CubeScratch sc(8 + ot::k_reduce_scratch(1));
+      ot::k_dot(F_phi, F_phi, (i64)(K + 1) * d.N, sc.dev + 0, sc.dev + 8, st);
+      ot::k_dot(F_rho, F_rho, (i64)K * d.N, sc.dev + 1, sc.dev + 8, st);
+      ot::k_dot(F_s, F_s, (i64)K * d.N, sc.dev + 2, sc.dev + 8, st);
+      double h3[3];
+      dev::copy_d2h(h3, sc.dev, 3 * sizeof(double), st);
+      dev::sync(st);
+      for (int i = 0; i < 3; ++i) norms[i] = sqrt(h3[i]);
+      norms[3] = sqrt(h3[0] + h3[1] + h3[2]);
+    }
+    dev::sync(st);
+    return OT_OK;
+  }
   Workspace& W = op_workspace(mesh, K);
   ot::k_residual(W.d, mu, phi, rho, s, rho_in, rho_f, F_phi, F_rho, F_s, st);
   if (norms) {
@@ -526,6 +574,13 @@ ot_status ot_kkt_apply(ot_mesh* mesh, int32_t K, const double* phi, const double
   OT_TRY
   require(mesh && phi && rho && s && rho_in && rho_f && x && y, "NULL argument");
   Stream st = cuda_stream;
+  if (is_cube(mesh)) {
+    require(K >= 1 && K <= 4096, "K must be in [1, 4096]");
+    CubeScratch sc(2 * (size_t)K + 2);
+    ot::k_cube_kkt_apply(ot::make_cube_dims(mesh->n, K), phi, rho, s, rho_in, rho_f, x, y, sc.dev, st);
+    dev::sync(st);
+    return OT_OK;
+  }
   Workspace& W = op_workspace(mesh, K);
   ot::k_kkt_coef(W.d, phi, rho, s, rho_in, rho_f, W.kcoef, st);
   ot::k_kkt_apply(W.d, W.kcoef, x, y, W.xmean, nullptr, st);
@@ -627,6 +682,17 @@ ot_status ot_cost_dual(ot_mesh* mesh, int32_t K, const double* phi, const double
   OT_TRY
   require(mesh && phi && rho && rho_in && rho_f, "NULL argument");
   Stream st = cuda_stream;
+  if (is_cube(mesh)) {
+    require(K >= 1 && K <= 4096, "K must be in [1, 4096]");
+    const ot::CubeDims d = ot::make_cube_dims(mesh->n, K);
+    CubeScratch sc(2 * (size_t)d.N + 2);
+    ot::k_cube_cost_dual(d, phi, rho, rho_in, rho_f, sc.dev + 2 * d.N, sc.dev, st);
+    dev::copy_d2h(sc.host, sc.dev + 2 * d.N, 2 * sizeof(double), st);
+    dev::sync(st);
+    if (cost) *cost = sc.host[0];
+    if (dual) *dual = sc.host[1];
+    return OT_OK;
+  }
   Workspace& W = op_workspace(mesh, K);
   ot::k_cost_dual(W.d, phi, rho, rho_in, rho_f, W.scal + 56, W.partial, st);
   dev::copy_d2h(W.host, W.scal + 56, 2 * sizeof(double), st);

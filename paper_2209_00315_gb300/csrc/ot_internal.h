@@ -314,6 +314,21 @@ void k_adjoint_rhs(const Dims& d, const double* phi, const double* rho, const do
                    double* rhs, double* gsum, Stream st);
 // grad_in, grad_f (N' each) from the adjoint potential lam ((K+1) x N).
 void k_adjoint_grad(const Dims& d, const double* phi, const double* lam, double* gin, double* gf, Stream st);
+// 3D Cartesian variant (k_cube.cu): n^3 cubes, J = I; operator level only.
+struct CubeDims {
+  int n, K;
+  i64 N;       // cells (= n^3, density and potential alike)
+  double h, V, T, dt;  // side, volume, face transmissibility |e|/|w| = h, 1/(K+1)
+};
+CubeDims make_cube_dims(int n, int K);
+void k_cube_residual(const CubeDims& d, double mu, const double* phi, const double* rho, const double* s,
+                     const double* r0, const double* r1, double* Fphi, double* Frho, double* Fs, Stream st);
+// y = projected KKT operator applied to x; scratch: 2 K doubles.
+void k_cube_kkt_apply(const CubeDims& d, const double* phi, const double* rho, const double* s, const double* r0,
+                      const double* r1, const double* x, double* y, double* scratch, Stream st);
+// out[0] = C, out[1] = D; scratch: 2 N doubles.
+void k_cube_cost_dual(const CubeDims& d, const double* phi, const double* rho, const double* r0, const double* r1,
+                      double* out, double* scratch, Stream st);
 // SIMPLE preconditioner pieces (k_simple.cu).  Ad ((K+1) N) = diagonal of the
 // potential block A from the KKT coefficients kc.
 void k_simple_diag(const Dims& d, const double* kc, double* Ad, Stream st);

@@ -90,6 +90,29 @@ def test_noalloc_entry_point_checks_arguments_before_device_work(lib_path):
     assert b"NULL" in lib.ot_last_error()
 
 
+def test_cube_meshes_report_their_grid_and_refuse_the_solver_calls(lib_path):
+    """The 3D Cartesian mesh (n^3 cubes, J = I) reports n^3 cells on both levels,
+    3 n^2 (n - 1) faces and cell volumes 1/n^3; every solver entry point returns
+    OT_ERR_INVALID_ARG for it before any device work."""
+    from paper_2209_00315_gb300 import capi
+
+    lib = capi.load()
+    m = capi.Mesh(5, kind="cube")
+    assert (m.n_coarse, m.n_fine, m.n_edges_fine) == (125, 125, 3 * 25 * 4)
+    assert abs(float(m.coarse_areas.sum()) - 1.0) < 1e-14
+    with pytest.raises(capi.OTError):
+        capi.Mesh(0, kind="cube")
+    o = capi.default_options()
+    p = ctypes.c_void_p(16)   # never dereferenced
+    st = capi.ot_stats()
+    assert lib.ot_ipm_solve(m.handle, p, p, 4, 1.0, 1e-6, ctypes.byref(o), 0, p, p, p, None, ctypes.byref(st),
+                            None) == 1
+    assert b"3D Cartesian" in lib.ot_last_error()
+    assert lib.ot_newton_solve(m.handle, 4, 0.1, p, p, p, p, p, ctypes.byref(o), p, p, p, None, None) == 1
+    assert lib.ot_bb_apply(m.handle, 4, ctypes.byref(o), p, p, p, p, p, p, p, None) == 1
+    assert b"3D Cartesian" in lib.ot_last_error()
+
+
 def test_solver_entry_points_check_arguments_before_allocating(lib_path):
     """Bad scalars, sizes and NULL arrays are rejected before any workspace is
     allocated, so these calls return OT_ERR_INVALID_ARG without a device."""
