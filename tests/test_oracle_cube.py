@@ -169,3 +169,46 @@ def test_cube_solution_respects_time_reversal_and_axis_permutations():
     for perm in (idx.transpose(0, 2, 1).ravel(), idx.transpose(2, 1, 0).ravel()):
         Rs = res.rho.reshape(K, -1)
         assert np.abs(Rs - Rs[:, perm]).max() < 1e-9 * np.abs(Rs).max()
+
+
+@pytest.mark.slow
+def test_cube_preconditioner_iteration_trends_along_the_barrier_path():
+    """Sec. 4.2-4.3 on the 3D variant, with exact inner solves: at the first Newton
+    step of each mu stage (4^3 cubes, K = 3, the 3D Gaussians) the BB-preconditioned
+    GMRES needs more iterations as mu decreases (measured 4 -> 13), and SIMPLE fewer
+    over the late stages, ending below BB (measured 15 at its peak -> 9)."""
+    from oracle import operators as ops
+    from test_oracle_pins import _gmres_right
+
+    n = 4
+    _, K, r0, r1 = cube_config_densities("gauss_cubeN", n)
+    d = ipm.discretise_cube(n, K)
+    opt = ipm.IPMOptions()
+    phi, rho, s = ipm.initial_point(d, r0, r1, opt.mu0)
+    mu = opt.mu0
+    bb, simple = [], []
+    for _ in range(ipm.stage_count(K, opt, d.area_total)):
+        F = ipm.residual(d, phi, rho, s, r0, r1, mu)
+        f0 = fn = ipm.residual_norm(F)
+        first = True
+        while fn > opt.newton_tol * max(1.0, f0):
+            if first:
+                Kp = d.projected_kkt(phi, rho, s, r0, r1)
+                gt = -F[1] + np.tile(d.t.coarse.area, K) * F[2] / rho
+                b = np.concatenate([-F[0], d.P_block() @ gt])
+                st = (phi, rho, s, r0, r1)
+                bb.append(_gmres_right(lambda x: Kp @ x, b, lambda v: np.concatenate(ops.bb_apply_exact(d, *st, v))))
+                simple.append(_gmres_right(lambda x: Kp @ x, b,
+                                           lambda v: np.concatenate(ops.simple_apply_exact(d, *st, v))))
+                first = False
+            dphi, drho, ds, _ = ipm.newton_direction(d, phi, rho, s, r0, r1, mu)
+            a = min(ipm.step_length(rho, drho, opt.tau), ipm.step_length(s, ds, opt.tau))
+            phi, rho, s = phi + a * dphi, ipm.renormalise(d, rho + a * drho, r0), s + a * ds
+            F = ipm.residual(d, phi, rho, s, r0, r1, mu)
+            fn = ipm.residual_norm(F)
+        mu *= opt.mu_factor
+    assert len(bb) == 10
+    assert all(b1 <= b2 for b1, b2 in zip(bb, bb[1:])) and bb[-1] >= 3 * bb[0]
+    peak = int(np.argmax(simple))
+    assert all(a >= b for a, b in zip(simple[peak:], simple[peak + 1:]))
+    assert simple[-1] < bb[-1]
